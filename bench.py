@@ -1,0 +1,288 @@
+"""Benchmark of the GB300 direct-volume-rendering path.
+
+Workload: the BrainWeb-shaped 181x217x181 uint16 T1 phantom rendered at
+1920x1080 (2D transfer function over intensity x gradient magnitude with
+curvature-modulated opacity, 8^3-brick empty-space skipping, step 0.5 voxel).
+A step is one frame: one vr_render call over the resident volume.
+
+  value  dense-equivalent Gsamples/s of the forward raymarch, inputs resident in
+         HBM, L2 flushed (256 MB write) between timed frames, CUDA events on
+         the context's stream, max over ranks, summed over ranks (weak scaling:
+         every rank renders its own orbit view of its own copy of the volume).
+  e2e    the same metric through the C ABI with host buffers: per frame the
+         tissue uniforms and transfer function are uploaded from host memory
+         and the image is copied back to pinned host memory.
+Run `python bench.py --impl reference` for the FP64 CPU oracle on the same
+workload (a bounded sample of the frame).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s & FPS at 1080p (fwd, fwd+bwd) vs plain fwd, % of HBM roofline"
+UNIT = "Gsamples/s"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 operations of one evaluated sample of the raymarch, counted from the
+# algorithm: 56-voxel separable contraction to I, grad, Hessian (368 incl. the
+# 4-tap weights), spacing scale (15), curvature/normalisation (38), transfer
+# function (2D bilinear, 36), Eq. 4 (8), Phong (16), Eqs. 5-6 (8), position (18).
+FLOPS_PER_SAMPLE = 507
+# Unique bytes a frame must move at least: the bricked voxels it touches (bounded
+# by the whole brick store) plus the RGBA float32 image it writes.
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        busy = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(busy)) if busy else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _json_line(d):
+    print(json.dumps(d), flush=True)
+
+
+def cpu_baseline(case, stride, threads=None):
+    """Time the FP64 oracle on every `stride`-th row/column of the frame."""
+    import oracle
+    from tests.gpu_util import oracle_params
+    if threads:
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    In = oracle.normalize(case["volume"])
+    t0 = time.perf_counter()
+    res = oracle.render(In, case["spacing"], oracle_params(case["params"], case["tf"]), case["tf"], case["cams"],
+                        case["W"], case["H"], pix_stride=stride, alternatives=False)
+    dt = time.perf_counter() - t0
+    dense = int(res.dense.sum())
+    rays = len(range(0, case["H"], stride)) * len(range(0, case["W"], stride))
+    return {"value": dense / dt / 1e9, "unit": UNIT, "cores": int(res.threads), "kind": "oracle",
+            "sample": "every %dth row and column of the 1920x1080 frame (%d rays, %d dense samples), "
+                      "including the oracle's voxel-derivative setup, %.1f s" % (stride, rays, dense, dt),
+            "seconds": dt, "dense_samples": dense}
+
+
+def run_reference(args):
+    from phantoms import workloads
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    case = workloads.brainweb_1080p()
+    stride = 6
+    vals, last = [], None
+    for i in range(args.warmup + args.steps):
+        last = cpu_baseline(case, stride)
+        if i >= args.warmup:
+            vals.append(last["value"])
+    v = float(np.mean(vals))
+    cb = dict(last, value=v)
+    _json_line({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * last["seconds"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": "brainweb_1080p", "volume": "181x217x181 u16",
+                                                "image": "1920x1080", "sample": cb["sample"]},
+                "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}})
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_19737_gb300 as pkg
+    from phantoms import cameras, workloads
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = workloads.brainweb_1080p(az=30.0 + 45.0 * rank)
+    W, H = case["W"], case["H"]
+    vol_np = case["volume"]
+    vol_host = torch.from_numpy(vol_np.view(np.int16)).pin_memory()
+    ctx = pkg.Context(local)
+
+    # Time-to-first-pixel analogue: host volume -> load -> morphology -> params -> first frame on the host.
+    img_host = torch.empty((1, H, W, 4), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vid0 = ctx.load_volume(vol_host, case["spacing"])
+    ctx.precompute_morphology(vid0)
+    ctx.set_tissue_params(vid0, case["tf"], **case["params"])
+    ctx.render(vid0, case["cams"], W, H, out=img_host)
+    ctx.synchronize()
+    ttfp_ms = 1000.0 * (time.perf_counter() - t0)
+    ctx.free_volume(vid0)
+
+    vid = ctx.load_volume(vol_host.to(dev), case["spacing"])
+    ctx.precompute_morphology(vid)
+    ctx.set_tissue_params(vid, case["tf"], **case["params"])
+    out = torch.empty((1, H, W, 4), dtype=torch.float32, device=dev)
+    ctr = pkg.new_counters(local)
+    ctx.render(vid, case["cams"], W, H, out=out, counters=ctr)
+    torch.cuda.synchronize()
+    rays, dense, evald = [int(x) for x in ctr.cpu().numpy()[:3]]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def frame():
+        ctx.render(vid, case["cams"], W, H, out=out)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        frame()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s, e in evs:
+        flush.zero_()
+        s.record()
+        frame()
+        e.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = float(np.mean([s.elapsed_time(e) for s, e in evs]))
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(dense)], device=dev, dtype=torch.float64)
+        dist.all_reduce(tot)
+        dense_all = float(tot.item())
+    else:
+        dense_all = float(dense)
+    value = dense_all / (ms * 1e-3) / 1e9
+
+    # End to end through the C ABI with host buffers: uniforms + TF from host, image back to pinned host.
+    tf_host = np.ascontiguousarray(case["tf"])
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.set_tissue_params(vid, tf_host, **case["params"])
+        ctx.render(vid, case["cams"], W, H, out=img_host)
+        ctx.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t1)
+    e2e_s = float(np.mean(e2e_times))
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = dense_all / e2e_s / 1e9
+
+    hbm, smax, peak_kind = _peaks()
+    nbricks = int(np.prod([(n - 1 + 7) // 8 for n in vol_np.shape]))
+    frame_bytes = nbricks * 6912 + W * H * 16
+    sm_mhz = clk.get("sm_mhz") or smax
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved_tflops = evald * FLOPS_PER_SAMPLE / (ms * 1e-3) / 1e12
+    if rank == 0:
+        cb = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline(workloads.brainweb_1080p(), stride=2)
+            cb.pop("seconds", None)
+        _json_line({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "brainweb_1080p", "volume": "181x217x181 u16 (BrainWeb-shaped phantom)",
+                       "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows",
+                       "step_vox": 0.5, "kernel": "gather", "l2": "flushed between frames (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "fps": 1000.0 / ms,
+            "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
+            "ttfp_ms": ttfp_ms,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / fp32_peak, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock under load)"
+                                        % sm_mhz},
+            "hbm_roofline": {"achieved": frame_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": frame_bytes / (ms * 1e-3) / 1e9 / hbm, "frac_vs_8tbs":
+                             frame_bytes / (ms * 1e-3) / 1e9 / 8000.0, "bytes_per_frame": frame_bytes,
+                             "peak_source": peak_kind},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tf_host.nbytes + 48),
+                    "d2h_bytes_per_step": int(W * H * 16), "ms_per_step": 1000.0 * e2e_s},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cb,
+        })
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * vr.h -- C ABI of the GB300 direct-volume-rendering library (libvr.so).
+ *
+ * The calls follow the problem statement of Beckley, "Decentralized Direct
+ * Volume Rendering: A Browser-Native GPU Architecture for MRI Digital Twins"
+ * (arXiv 2605.19737): a volume is loaded with its dims and spacing and
+ * min-max normalised (Sec. 2.2, Eq. 1); its morphology is precomputed once
+ * (Sec. 2.3; the multi-scale Hessian vesselness of Sec. 1); tissue windows and
+ * transfer-function uniforms change without recomputation (abstract, Sec. 4,
+ * Sec. 5.4); a single-pass front-to-back raymarch turns a camera into an RGBA
+ * image (Sec. 2.4, Eqs. 4-6); and an adjoint raymarch returns gradients of a
+ * loss on that image.
+ *
+ * Conventions shared by every call:
+ *   - Volumes are dense, x fastest: voxel (i,j,k) at (k*ny + j)*nx + i, its
+ *     centre at ((i+.5)sx, (j+.5)sy, (k+.5)sz) in mm; the volume fills the box
+ *     [0, nx sx] x [0, ny sy] x [0, nz sz]. 2 <= nx, ny, nz <= 2048.
+ *   - Images are premultiplied RGBA float32, [n_cams][H][W][4], row 0 = top,
+ *     black transparent background.
+ *   - Ownership: the caller owns every buffer it passes; the library copies
+ *     what it keeps (volume, transfer function) into device memory it owns
+ *     and frees in vr_free_volume / vr_destroy.
+ *   - Pointers named d_* are device pointers on the context's device; h_* are
+ *     host pointers; others say which in their comment.
+ *   - Asynchrony: work is enqueued on the context's CUDA stream. Argument
+ *     errors return at once; errors raised by kernels surface at the next
+ *     vr_synchronize (or at a call that must read results back).
+ *   - No call aborts, throws or prints. On failure the returned status is
+ *     non-zero and vr_last_error(ctx) describes it.
+ *   - One context per host thread; a context is not thread-safe.
+ */
+#ifndef VR_H
+#define VR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VR_ABI_VERSION 1
+
+typedef struct vr_ctx vr_ctx;
+
+typedef enum {
+    VR_OK = 0,
+    VR_ERR_INVALID_ARG = 1, /* bad pointer, size, id or parameter value */
+    VR_ERR_NOT_READY = 2,   /* a required earlier call has not been made */
+    VR_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel failed */
+    VR_ERR_OOM = 4,         /* device allocation failed */
+    VR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    VR_ERR_DEGENERATE = 6   /* I_max == I_min: Eq. 1 is undefined */
+} vr_status;
+
+typedef enum { VR_F32 = 0, VR_U16 = 1 } vr_dtype;
+
+/* A pinhole camera. fwd is the unit viewing direction; right and up are
+ * pre-scaled by tan(fov/2)*aspect and tan(fov/2), so pixel (i, j) looks along
+ * normalize(fwd + a*right + b*up), a = 2(i+1/2)/W - 1, b = 1 - 2(j+1/2)/H. */
+typedef struct {
+    float eye[3];
+    float fwd[3];
+    float right[3];
+    float up[3];
+} vr_camera;
+
+typedef enum {
+    VR_TF_1D = 0,        /* opacity/colour over I_norm (tf_h == 1) */
+    VR_TF_2D_GRAD = 1,   /* over (I_norm, |grad I| / |grad I|_max) */
+    VR_TF_2D_VESSEL = 2  /* over (I_norm, vesselness V); needs vesselness */
+} vr_tf_mode;
+
+/* Tissue and transfer-function uniforms (Sec. 2.4, Eq. 4; Table 2 windows are
+ * encoded in the table). Per sample at normalised intensity I:
+ *   (r,g,b,a) = tf(I [, second axis])         piecewise-linear lookup
+ *   m_g       = grad_mod ? min(|g|/|g|max, 1) : 1
+ *   w(kappa)  = clamp(1 + gamma*kappa/kappa_ref, 0, w_max),  kappa = g^T H g/|g|^2
+ *   alpha     = clamp(opacity_scale * a * m_g * w, 0, 1)     (Eq. 4)
+ *   colour    = shading ? rgb*(ka + kd*d) + ks*d^16 : rgb,   d = |g/|g| . dir|
+ * Samples are spaced step_vox * min(s) mm apart (step_vox in [0.01, 16]); a ray stops after the first
+ * sample whose accumulated opacity reaches et_threshold (> 1 disables). */
+typedef struct {
+    int tf_mode;        /* vr_tf_mode */
+    int tf_w;           /* entries along I_norm, 2..4096 (256 typical) */
+    int tf_h;           /* entries along the second axis: 1 for 1D, 2..256 for 2D */
+    const float* tf;    /* [tf_h][tf_w][4] RGBA float32; host or device (tf_on_device) */
+    int tf_on_device;
+    int grad_mod;       /* 0 or 1 */
+    int shading;        /* 0 or 1 */
+    float gamma, kappa_ref, w_max;
+    float ka, kd, ks;
+    float opacity_scale, et_threshold, step_vox;
+} vr_tissue_params;
+
+/* Device-side counters a render may add into (zero them yourself first). */
+typedef struct {
+    unsigned long long rays;              /* rays that hit the volume box */
+    unsigned long long dense_samples;     /* sample points up to each ray's stop */
+    unsigned long long evaluated_samples; /* of those, not in skipped bricks */
+    unsigned long long bricks_staged;     /* brick copies into shared memory */
+} vr_counters;
+
+typedef enum {
+    VR_KERNEL_AUTO = 0,    /* the fastest available (staged) */
+    VR_KERNEL_GATHER = 1,  /* per-lane gathers from the bricked volume in HBM/L2 */
+    VR_KERNEL_STAGED = 2   /* warp-cooperative brick staging in shared memory */
+} vr_kernel;
+
+typedef struct {
+    int kernel;         /* vr_kernel */
+    int skip_empty;     /* 1: skip bricks classified empty (bit-neutral) */
+    int packet_w;       /* staged kernel: rays per packet along x (packet = 32 rays) */
+    int warps_per_block;/* staged kernel: warps per CTA, 1..16 */
+} vr_render_opts;
+
+/* ------------------------------------------------------------------ context */
+
+/* Library version string, e.g. "vr 1.0 sm_103a". Never NULL. */
+const char* vr_version(void);
+
+/* Create a context on CUDA device `device` that enqueues its work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the context. Errors: INVALID_ARG (out NULL, bad device), CUDA. */
+vr_status vr_create(vr_ctx** out, int device, void* cuda_stream);
+
+/* Synchronise, free every buffer the context owns, destroy it. NULL is a no-op. */
+vr_status vr_destroy(vr_ctx* ctx);
+
+/* Switch the stream later calls enqueue on. */
+vr_status vr_set_stream(vr_ctx* ctx, void* cuda_stream);
+
+/* Wait for the context's stream; report asynchronous kernel errors and the
+ * device status word (TIMEOUT if a bounded wait expired). */
+vr_status vr_synchronize(vr_ctx* ctx);
+
+/* Message for the last non-OK status of this context ("" if none). */
+const char* vr_last_error(vr_ctx* ctx);
+
+/* ------------------------------------------------------------------ volumes */
+
+/* Load a volume (Sec. 2.1 ingestion, Sec. 2.2 Eq. 1).
+ *   data: nx*ny*nz values of `dtype`, x fastest; on the device if on_device,
+ *         else in host memory (pinned memory makes the copy asynchronous).
+ * The library copies the data, computes I_min/I_max with a parallel
+ * reduction, writes the normalised volume and its 8^3-cell bricks (stored
+ * 12^3 with a clamp-to-edge apron) and the quantised per-brick min/max grid.
+ * *vol_id receives the volume's id. Synchronises once to check Eq. 1.
+ * Errors: INVALID_ARG (dims outside [2, 2048], spacing <= 0 or not finite,
+ * NULL pointers), DEGENERATE (I_max == I_min), OOM, CUDA. */
+vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype dtype, int nx, int ny, int nz,
+                         float sx, float sy, float sz, int* vol_id);
+
+/* Free a volume and everything derived from it. */
+vr_status vr_free_volume(vr_ctx* ctx, int vol_id);
+
+/* Per-volume morphology (Sec. 2.3 and Sec. 1), run once per volume:
+ * |grad I|_max over voxels (Eq. 4's normaliser, a parallel reduction), and,
+ * when n_sigmas > 0, the multi-scale Frangi vesselness V = max over
+ * h_sigmas[0..n_sigmas-1] (voxel units, each in (0, 8]) of the bright-vessel
+ * response of the sigma^2-scaled Hessian of the Gaussian-smoothed volume,
+ * alpha = beta = 0.5, c = half the largest Hessian norm at that scale.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigmas, int n_sigmas);
+
+/* Set transfer-function and tissue uniforms (copied), then re-classify the
+ * bricks for empty-space skipping. Nothing else is recomputed (the uniform
+ * buffers of the abstract and Sec. 4). Errors: INVALID_ARG (bad sizes or
+ * values, 2D-vessel mode without vesselness), NOT_READY, OOM, CUDA. */
+vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* tp);
+
+/* I_min, I_max (Eq. 1) and |grad I|_max (Eq. 4) of a volume; any pointer may be
+ * NULL. Reads back from the device (synchronises). gmax is 0 before
+ * vr_precompute_morphology. */
+vr_status vr_get_norm(vr_ctx* ctx, int vol_id, float* imin, float* imax, float* gmax);
+
+/* Override |grad I|_max (e.g. to hold it fixed while a test perturbs voxels). */
+vr_status vr_set_gmax(vr_ctx* ctx, int vol_id, float gmax);
+
+/* Overwrite the normalised intensities of a loaded volume with
+ * d_norm[nx*ny*nz] (device, float32, x fastest) and rebuild its bricks and
+ * min/max grid; I_min/I_max and |grad I|_max are kept. Used to render or
+ * differentiate a volume given directly in I_norm units. */
+vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm);
+
+/* Copy derived data to host memory (synchronises):
+ *   h_grid: nbx*nby*nbz*2 uint16 (qlo, qhi) per brick, nb = ceil((n-1)/8);
+ *   h_empty: nbx*nby*nbz bytes, 1 = brick skipped under the current params;
+ *   h_nb: 3 ints (nbx, nby, nbz). Any of them may be NULL. */
+vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb);
+
+/* Copy the vesselness volume (nx*ny*nz float32) to `out` (device if
+ * out_on_device, else host; synchronises for host). NOT_READY without it. */
+vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_device);
+
+/* Copy the normalised volume (nx*ny*nz float32) to `out` (as above). */
+vr_status vr_get_normalized(vr_ctx* ctx, int vol_id, float* out, int out_on_device);
+
+/* Global min and max of n values (the parallel reduction of Sec. 4 applied to
+ * Eq. 1's I_min, I_max): d_data holds n values of `dtype` on the device;
+ * d_out2[0] = min, d_out2[1] = max as float32 (device). Asynchronous; uses
+ * partial results in scratch memory the context owns (allocated on first
+ * use, grown as needed). Errors: INVALID_ARG (n < 1, NULL), OOM, CUDA. */
+vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long long n, float* d_out2);
+
+/* ---------------------------------------------------------------- rendering */
+
+/* Render n_cams images (Sec. 2.4): per pixel one ray, samples at
+ * t_near + (k+1/2) dt, per sample the trilinear field and its gradient and
+ * Hessian (Eqs. 2-3), opacity by Eq. 4, front-to-back compositing by
+ * Eqs. 5-6, early termination, and empty-space skipping.
+ *   h_cams: n_cams cameras in host memory (copied at launch).
+ *   out_rgba: n_cams*H*W*4 float32 -- device memory, or host memory when
+ *             out_on_host (then the image is copied back on the stream).
+ *   opts: NULL for defaults (fastest kernel, skipping on).
+ *   d_counters: NULL or device vr_counters to add into.
+ *   d_ray_samples: NULL or device uint32 [n_cams][H][W][2] receiving each
+ *             ray's dense and evaluated sample counts.
+ * Errors: INVALID_ARG (n_cams < 1, W or H outside [1, 16384]), NOT_READY
+ * (no vr_precompute_morphology or vr_set_tissue_params yet), OOM, CUDA. */
+vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
+                    int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
+                    unsigned int* d_ray_samples);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VR_H */

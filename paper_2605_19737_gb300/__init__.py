@@ -1,0 +1,208 @@
+"""GB300-native direct volume rendering of MRI volumes (arXiv 2605.19737, Sec. 2.2-2.4).
+
+``Context`` wraps the C ABI of libvr.so (include/vr.h) for torch/numpy
+buffers; device memory comes from torch, every computation from the
+library's CUDA kernels. There is no CPU path: without a GPU or without the
+built library these calls raise.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import vr as _vr
+from .vr import (  # noqa: F401
+    VR_F32, VR_U16, VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL,
+    VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED,
+    vr_camera, vr_tissue_params, vr_counters, vr_render_opts,
+)
+
+
+class VRError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_vr.STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    if stream is None:
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    """(address, on_device) of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, False
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr(), x.is_cuda
+
+
+def cameras_to_c(cams):
+    """(n, 12) float32 camera rows -> ctypes array of vr_camera."""
+    c = np.ascontiguousarray(np.asarray(cams, np.float32).reshape(-1, 12))
+    arr = (vr_camera * c.shape[0])()
+    ctypes.memmove(arr, c.ctypes.data, c.nbytes)
+    return arr, c.shape[0]
+
+
+class Context:
+    """One vr_ctx bound to a CUDA device and stream (torch's current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        self._lib = _vr.load()
+        h = ctypes.c_void_p()
+        st = self._lib.vr_create(ctypes.byref(h), int(device), _stream_handle(stream))
+        if st != 0:
+            raise VRError(st, "vr_create failed")
+        self._h = h
+        self.device = int(device)
+        self._keep = {}
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, st):
+        if st != 0:
+            msg = self._lib.vr_last_error(self._h)
+            raise VRError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.vr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        self._check(self._lib.vr_set_stream(self._h, _stream_handle(stream)))
+
+    def synchronize(self):
+        self._check(self._lib.vr_synchronize(self._h))
+
+    # -- volumes ----------------------------------------------------------
+    def reduce_minmax(self, data, out=None):
+        torch = _torch()
+        dtype = VR_F32 if data.dtype == torch.float32 else VR_U16
+        if out is None:
+            out = torch.empty(2, dtype=torch.float32, device=data.device)
+        p, _ = _ptr(data)
+        self._check(self._lib.vr_reduce_minmax(self._h, p, dtype, data.numel(), out.data_ptr()))
+        return out
+
+    def load_volume(self, data, spacing=(1.0, 1.0, 1.0)):
+        """data: (nz, ny, nx) float32 or uint16 (int16 tensors are read as uint16), host or device."""
+        if isinstance(data, np.ndarray):
+            dt = VR_F32 if data.dtype == np.float32 else (VR_U16 if data.dtype == np.uint16 else None)
+        else:
+            torch = _torch()
+            dt = VR_F32 if data.dtype == torch.float32 else (
+                VR_U16 if data.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)) else None)
+        if dt is None:
+            raise TypeError("volume must be float32 or uint16")
+        nz, ny, nx = data.shape
+        p, dev = _ptr(data)
+        vid = ctypes.c_int()
+        self._check(self._lib.vr_load_volume(self._h, p, int(dev), dt, nx, ny, nz, float(spacing[0]),
+                                             float(spacing[1]), float(spacing[2]), ctypes.byref(vid)))
+        self._keep[vid.value] = (nx, ny, nz)
+        return vid.value
+
+    def dims(self, vol):
+        return self._keep[vol]
+
+    def free_volume(self, vol):
+        self._check(self._lib.vr_free_volume(self._h, vol))
+        self._keep.pop(vol, None)
+
+    def precompute_morphology(self, vol, sigmas=()):
+        s = np.ascontiguousarray(np.asarray(sigmas, np.float32))
+        self._check(self._lib.vr_precompute_morphology(self._h, vol, s.ctypes.data if s.size else None, s.size))
+
+    def set_tissue_params(self, vol, tf, tf_mode=0, grad_mod=1, shading=0, gamma=0.0, kappa_ref=1.0, w_max=4.0,
+                          ka=0.3, kd=0.7, ks=0.2, opacity_scale=1.0, et_threshold=0.99, step_vox=0.5):
+        """tf: (h, w, 4) float32 RGBA table, numpy (host) or torch (host or device)."""
+        if isinstance(tf, np.ndarray):
+            tf = np.ascontiguousarray(tf, np.float32)
+        else:
+            tf = tf.contiguous()
+        h, w = int(tf.shape[0]), int(tf.shape[1])
+        p, dev = _ptr(tf)
+        tp = vr_tissue_params(int(tf_mode), w, h, p, int(dev), int(grad_mod), int(shading), gamma, kappa_ref,
+                              w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox)
+        self._check(self._lib.vr_set_tissue_params(self._h, vol, ctypes.byref(tp)))
+
+    def get_norm(self, vol):
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        self._check(self._lib.vr_get_norm(self._h, vol, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_gmax(self, vol, gmax):
+        self._check(self._lib.vr_set_gmax(self._h, vol, float(gmax)))
+
+    def set_normalized(self, vol, norm):
+        self._check(self._lib.vr_set_normalized(self._h, vol, norm.contiguous().data_ptr()))
+
+    def get_bricks(self, vol):
+        nb = (ctypes.c_int * 3)()
+        self._check(self._lib.vr_get_bricks(self._h, vol, None, None, nb))
+        nbx, nby, nbz = nb[0], nb[1], nb[2]
+        grid = np.zeros((nbz, nby, nbx, 2), np.uint16)
+        empty = np.zeros((nbz, nby, nbx), np.uint8)
+        self._check(self._lib.vr_get_bricks(self._h, vol, grid.ctypes.data, empty.ctypes.data, nb))
+        return grid, empty
+
+    def get_normalized(self, vol):
+        torch = _torch()
+        nx, ny, nz = self._keep[vol]
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda:%d" % self.device)
+        self._check(self._lib.vr_get_normalized(self._h, vol, out.data_ptr(), 1))
+        return out
+
+    def get_vesselness(self, vol):
+        torch = _torch()
+        nx, ny, nz = self._keep[vol]
+        out = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda:%d" % self.device)
+        self._check(self._lib.vr_get_vesselness(self._h, vol, out.data_ptr(), 1))
+        return out
+
+    # -- rendering ----------------------------------------------------------
+    def render(self, vol, cams, W, H, out=None, kernel=VR_KERNEL_AUTO, skip_empty=True, packet_w=8,
+               warps_per_block=4, counters=None, ray_samples=None):
+        """Render (n, H, W, 4) premultiplied RGBA. ``out`` may be a device tensor or a
+        pinned host tensor (then the library copies the image back on the stream)."""
+        torch = _torch()
+        carr, n = cameras_to_c(cams)
+        if out is None:
+            out = torch.empty((n, H, W, 4), dtype=torch.float32, device="cuda:%d" % self.device)
+        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), int(warps_per_block))
+        p, dev = _ptr(out)
+        self._check(self._lib.vr_render(self._h, vol, carr, n, W, H, p, int(not dev), ctypes.byref(opts),
+                                        counters.data_ptr() if counters is not None else None,
+                                        ray_samples.data_ptr() if ray_samples is not None else None))
+        return out
+
+
+def new_counters(device=0):
+    """Zeroed device vr_counters as a (4,) int64 tensor (rays, dense, evaluated, staged)."""
+    torch = _torch()
+    return torch.zeros(4, dtype=torch.int64, device="cuda:%d" % device)

@@ -1,0 +1,491 @@
+// vr_api.cu -- the C ABI declared in include/vr.h: contexts, volume registry,
+// argument checking, device-memory ownership and launch orchestration. Every
+// step of the rendering path runs in this library's kernels; this file only
+// validates, allocates and enqueues.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+
+#include "vr_internal.cuh"
+
+using namespace vr;
+
+namespace {
+
+struct Volume {
+    int n[3] = {0, 0, 0};
+    int nb[3] = {0, 0, 0};
+    float s[3] = {1, 1, 1};
+    long long nvox = 0, nbricks = 0;
+    float* d_norm = nullptr;
+    float* d_bricks = nullptr;
+    uint16_t* d_grid = nullptr;
+    uint8_t* d_empty = nullptr;
+    VolConst* d_vc = nullptr;
+    float* d_minmax = nullptr;
+    float* d_vessel = nullptr;
+    float* d_vbricks = nullptr;
+    float* d_tf = nullptr;
+    size_t tf_cap = 0;
+    int* d_prefix = nullptr;
+    int prefix_cap = 0;
+    TissueDev tp{};
+    bool morph_ready = false, params_ready = false;
+};
+
+}  // namespace
+
+struct vr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::map<int, Volume*> vols;
+    int next_id = 1;
+    float* d_partials = nullptr;
+    int partials_cap = 0;
+    void* d_stage = nullptr;
+    size_t stage_cap = 0;
+    unsigned* d_work = nullptr;
+};
+
+namespace {
+
+vr_status fail(vr_ctx* c, vr_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+vr_status fail(vr_ctx* c, vr_status s, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+vr_status cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return VR_OK;
+    (void)cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t bytes) {
+    return cudaMalloc((void**)p, bytes);
+}
+
+void free_volume(Volume* v) {
+    cudaFree(v->d_norm);
+    cudaFree(v->d_bricks);
+    cudaFree(v->d_grid);
+    cudaFree(v->d_empty);
+    cudaFree(v->d_vc);
+    cudaFree(v->d_minmax);
+    cudaFree(v->d_vessel);
+    cudaFree(v->d_vbricks);
+    cudaFree(v->d_tf);
+    cudaFree(v->d_prefix);
+    delete v;
+}
+
+Volume* get_vol(vr_ctx* ctx, int id) {
+    auto it = ctx->vols.find(id);
+    return it == ctx->vols.end() ? nullptr : it->second;
+}
+
+cudaError_t ensure_stage(vr_ctx* ctx, size_t bytes) {
+    if (ctx->stage_cap >= bytes) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return e;
+    cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_cap = 0;
+    e = cudaMalloc(&ctx->d_stage, bytes);
+    if (e == cudaSuccess) ctx->stage_cap = bytes;
+    return e;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
+
+vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
+    CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
+    CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
+    return VR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vr_version(void) { return "vr 1.0 sm_103a"; }
+
+vr_status vr_create(vr_ctx** out, int device, void* cuda_stream) {
+    if (!out) return VR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return VR_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return VR_ERR_INVALID_ARG;
+    vr_ctx* ctx = new vr_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    cudaError_t e = cudaMalloc(&ctx->d_work, 64 * sizeof(unsigned));
+    if (e != cudaSuccess) {
+        delete ctx;
+        (void)cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+    }
+    *out = ctx;
+    return VR_OK;
+}
+
+vr_status vr_destroy(vr_ctx* ctx) {
+    if (!ctx) return VR_OK;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->vols) free_volume(kv.second);
+    cudaFree(ctx->d_partials);
+    cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_work);
+    (void)cudaGetLastError();
+    delete ctx;
+    return VR_OK;
+}
+
+vr_status vr_set_stream(vr_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return VR_OK;
+}
+
+vr_status vr_synchronize(vr_ctx* ctx) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    CK(cudaGetLastError(), "asynchronous error");
+    return VR_OK;
+}
+
+const char* vr_last_error(vr_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long long n, float* d_out2) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!d_data || !d_out2 || n < 1) return fail(ctx, VR_ERR_INVALID_ARG, "reduce_minmax: bad arguments");
+    if (dtype != VR_F32 && dtype != VR_U16) return fail(ctx, VR_ERR_INVALID_ARG, "reduce_minmax: bad dtype");
+    DeviceGuard g(ctx->device);
+    const int nblocks = minmax_blocks(n);
+    if (ctx->partials_cap < nblocks) {
+        CK(cudaStreamSynchronize(ctx->stream), "reduce_minmax sync");
+        cudaFree(ctx->d_partials);
+        ctx->d_partials = nullptr;
+        ctx->partials_cap = 0;
+        CK(dalloc(&ctx->d_partials, sizeof(float) * 2 * nblocks), "reduce_minmax scratch");
+        ctx->partials_cap = nblocks;
+    }
+    CK(launch_minmax_partials(d_data, dtype, n, ctx->d_partials, nblocks, ctx->stream), "minmax partials");
+    CK(launch_minmax_final(ctx->d_partials, nblocks, d_out2, ctx->stream), "minmax final");
+    return VR_OK;
+}
+
+vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype dtype, int nx, int ny, int nz,
+                         float sx, float sy, float sz, int* vol_id) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!data || !vol_id) return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: NULL pointer");
+    if (dtype != VR_F32 && dtype != VR_U16) return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: bad dtype");
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 2048 || ny > 2048 || nz > 2048)
+        return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: dims %d x %d x %d outside [2, 2048]", nx, ny, nz);
+    if (!finite_pos(sx) || !finite_pos(sy) || !finite_pos(sz))
+        return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: spacing must be finite and > 0");
+    DeviceGuard g(ctx->device);
+    Volume* v = new Volume();
+    v->n[0] = nx, v->n[1] = ny, v->n[2] = nz;
+    v->s[0] = sx, v->s[1] = sy, v->s[2] = sz;
+    for (int a = 0; a < 3; ++a) v->nb[a] = (v->n[a] - 1 + kCells - 1) / kCells;
+    v->nvox = (long long)nx * ny * nz;
+    v->nbricks = (long long)v->nb[0] * v->nb[1] * v->nb[2];
+    const size_t esz = dtype == VR_F32 ? 4 : 2;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dalloc(&v->d_norm, sizeof(float) * v->nvox);
+    if (e == cudaSuccess) e = dalloc(&v->d_bricks, (size_t)kBrickBytes * v->nbricks);
+    if (e == cudaSuccess) e = dalloc(&v->d_grid, sizeof(uint16_t) * 2 * v->nbricks);
+    if (e == cudaSuccess) e = dalloc(&v->d_empty, v->nbricks);
+    if (e == cudaSuccess) e = dalloc(&v->d_vc, sizeof(VolConst));
+    if (e == cudaSuccess) e = dalloc(&v->d_minmax, 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_vc, 0, sizeof(VolConst), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->d_empty, 0, v->nbricks, ctx->stream);
+    const void* raw = data;
+    if (e == cudaSuccess && !on_device) {
+        e = ensure_stage(ctx, esz * v->nvox);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_stage, data, esz * v->nvox, cudaMemcpyHostToDevice, ctx->stream);
+        raw = ctx->d_stage;
+    }
+    if (e != cudaSuccess) {
+        free_volume(v);
+        return cuda_fail(ctx, e, "load_volume: allocate/copy");
+    }
+    vr_status st = vr_reduce_minmax(ctx, raw, dtype, v->nvox, v->d_minmax);
+    if (st == VR_OK) {
+        e = launch_normalize(raw, dtype, v->nvox, v->d_minmax, v->d_vc, v->d_norm, ctx->stream);
+        st = cuda_fail(ctx, e, "normalize");
+    }
+    if (st == VR_OK) st = rebuild_bricks(ctx, v);
+    float mm[2] = {0, 0};
+    if (st == VR_OK) {
+        e = cudaMemcpyAsync(mm, v->d_minmax, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        st = cuda_fail(ctx, e, "load_volume: read back I_min/I_max");
+    }
+    if (st == VR_OK && !(mm[1] > mm[0])) {
+        st = fail(ctx, VR_ERR_DEGENERATE, "load_volume: I_max == I_min (%g); Eq. 1 undefined", (double)mm[0]);
+    }
+    if (st == VR_OK && !(isfinite(mm[0]) && isfinite(mm[1])))
+        st = fail(ctx, VR_ERR_INVALID_ARG, "load_volume: non-finite intensities");
+    if (st != VR_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        free_volume(v);
+        return st;
+    }
+    const int id = ctx->next_id++;
+    ctx->vols[id] = v;
+    *vol_id = id;
+    return VR_OK;
+}
+
+vr_status vr_free_volume(vr_ctx* ctx, int vol_id) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "free_volume: unknown id %d", vol_id);
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_volume(v);
+    ctx->vols.erase(vol_id);
+    return VR_OK;
+}
+
+vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigmas, int n_sigmas) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: unknown id %d", vol_id);
+    if (n_sigmas < 0 || n_sigmas > 8 || (n_sigmas > 0 && !h_sigmas))
+        return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: bad sigma list");
+    for (int i = 0; i < n_sigmas; ++i)
+        if (!(h_sigmas[i] > 0.0f && h_sigmas[i] <= 8.0f))
+            return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: sigma %g outside (0, 8]", (double)h_sigmas[i]);
+    if (n_sigmas > 0) return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: vesselness not built yet");
+    DeviceGuard g(ctx->device);
+    CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
+    v->morph_ready = true;
+    return VR_OK;
+}
+
+vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* tp) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: unknown id %d", vol_id);
+    if (!tp || !tp->tf) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: NULL pointer");
+    if (tp->tf_mode < 0 || tp->tf_mode > 2) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: bad tf_mode");
+    if (tp->tf_w < 2 || tp->tf_w > 4096) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: tf_w outside [2, 4096]");
+    if (tp->tf_mode == 0 ? tp->tf_h != 1 : (tp->tf_h < 2 || tp->tf_h > 256))
+        return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: tf_h %d invalid for mode %d", tp->tf_h, tp->tf_mode);
+    if (tp->tf_mode == 2 && !v->d_vessel)
+        return fail(ctx, VR_ERR_NOT_READY, "set_tissue_params: vesselness mode needs precomputed vesselness");
+    if (!finite_pos(tp->kappa_ref) || !(tp->w_max >= 0.0f) || !isfinite(tp->gamma) || !finite_pos(tp->step_vox) ||
+        !(tp->opacity_scale >= 0.0f) || !isfinite(tp->opacity_scale) || !isfinite(tp->et_threshold) ||
+        !isfinite(tp->ka) || !isfinite(tp->kd) || !isfinite(tp->ks))
+        return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: bad scalar parameter");
+    if (!(tp->step_vox >= 0.01f && tp->step_vox <= 16.0f))
+        return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: step_vox %g outside [0.01, 16]", (double)tp->step_vox);
+    if ((tp->grad_mod != 0 && tp->grad_mod != 1) || (tp->shading != 0 && tp->shading != 1))
+        return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: grad_mod/shading must be 0 or 1");
+    DeviceGuard g(ctx->device);
+    const size_t bytes = sizeof(float) * 4 * (size_t)tp->tf_w * tp->tf_h;
+    if (v->tf_cap < bytes) {
+        CK(cudaStreamSynchronize(ctx->stream), "set_tissue_params sync");
+        cudaFree(v->d_tf);
+        v->d_tf = nullptr;
+        v->tf_cap = 0;
+        CK(dalloc(&v->d_tf, bytes), "transfer function");
+        v->tf_cap = bytes;
+    }
+    if (v->prefix_cap < tp->tf_w + 1) {
+        CK(cudaStreamSynchronize(ctx->stream), "set_tissue_params sync");
+        cudaFree(v->d_prefix);
+        v->d_prefix = nullptr;
+        v->prefix_cap = 0;
+        CK(dalloc(&v->d_prefix, sizeof(int) * (tp->tf_w + 1)), "classification scratch");
+        v->prefix_cap = tp->tf_w + 1;
+    }
+    CK(cudaMemcpyAsync(v->d_tf, tp->tf, bytes, tp->tf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "transfer function copy");
+    TissueDev& d = v->tp;
+    d.tf_mode = tp->tf_mode, d.tf_w = tp->tf_w, d.tf_h = tp->tf_h;
+    d.grad_mod = tp->grad_mod, d.shading = tp->shading;
+    d.gamma = tp->gamma, d.kappa_ref = tp->kappa_ref, d.w_max = tp->w_max;
+    d.ka = tp->ka, d.kd = tp->kd, d.ks = tp->ks;
+    d.opacity_scale = tp->opacity_scale, d.et_threshold = tp->et_threshold, d.step_vox = tp->step_vox;
+    CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, tp->tf_w, tp->tf_h, v->d_empty, v->d_prefix, ctx->stream),
+       "classify");
+    v->params_ready = true;
+    return VR_OK;
+}
+
+vr_status vr_get_norm(vr_ctx* ctx, int vol_id, float* imin, float* imax, float* gmax) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "get_norm: unknown id %d", vol_id);
+    DeviceGuard g(ctx->device);
+    VolConst vc;
+    CK(cudaMemcpyAsync(&vc, v->d_vc, sizeof vc, cudaMemcpyDeviceToHost, ctx->stream), "get_norm copy");
+    CK(cudaStreamSynchronize(ctx->stream), "get_norm sync");
+    if (imin) *imin = vc.imin;
+    if (imax) *imax = vc.imax;
+    if (gmax) *gmax = vc.gmax;
+    return VR_OK;
+}
+
+vr_status vr_set_gmax(vr_ctx* ctx, int vol_id, float gmax) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "set_gmax: unknown id %d", vol_id);
+    if (!finite_pos(gmax)) return fail(ctx, VR_ERR_INVALID_ARG, "set_gmax: must be finite and > 0");
+    DeviceGuard g(ctx->device);
+    static_assert(sizeof(float) == 4, "float");
+    // A host value copied on the stream: stage it through a pageable copy (synchronous for the host).
+    CK(cudaMemcpyAsync(&v->d_vc->gmax, &gmax, sizeof(float), cudaMemcpyHostToDevice, ctx->stream), "set_gmax copy");
+    CK(cudaStreamSynchronize(ctx->stream), "set_gmax sync");
+    v->morph_ready = true;
+    return VR_OK;
+}
+
+vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v || !d_norm) return fail(ctx, VR_ERR_INVALID_ARG, "set_normalized: bad arguments");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(v->d_norm, d_norm, sizeof(float) * v->nvox, cudaMemcpyDeviceToDevice, ctx->stream),
+       "set_normalized copy");
+    vr_status st = rebuild_bricks(ctx, v);
+    if (st != VR_OK) return st;
+    if (v->params_ready)
+        CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix,
+                           ctx->stream),
+           "classify");
+    return VR_OK;
+}
+
+vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "get_bricks: unknown id %d", vol_id);
+    DeviceGuard g(ctx->device);
+    if (h_grid)
+        CK(cudaMemcpyAsync(h_grid, v->d_grid, sizeof(uint16_t) * 2 * v->nbricks, cudaMemcpyDeviceToHost, ctx->stream),
+           "get_bricks grid");
+    if (h_empty) CK(cudaMemcpyAsync(h_empty, v->d_empty, v->nbricks, cudaMemcpyDeviceToHost, ctx->stream), "get_bricks flags");
+    CK(cudaStreamSynchronize(ctx->stream), "get_bricks sync");
+    if (h_nb)
+        for (int a = 0; a < 3; ++a) h_nb[a] = v->nb[a];
+    return VR_OK;
+}
+
+vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_device) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v || !out) return fail(ctx, VR_ERR_INVALID_ARG, "get_vesselness: bad arguments");
+    if (!v->d_vessel) return fail(ctx, VR_ERR_NOT_READY, "get_vesselness: no vesselness computed");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(out, v->d_vessel, sizeof(float) * v->nvox,
+                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+       "get_vesselness copy");
+    if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream), "get_vesselness sync");
+    return VR_OK;
+}
+
+vr_status vr_get_normalized(vr_ctx* ctx, int vol_id, float* out, int out_on_device) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v || !out) return fail(ctx, VR_ERR_INVALID_ARG, "get_normalized: bad arguments");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(out, v->d_norm, sizeof(float) * v->nvox,
+                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+       "get_normalized copy");
+    if (!out_on_device) CK(cudaStreamSynchronize(ctx->stream), "get_normalized sync");
+    return VR_OK;
+}
+
+vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
+                    int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
+                    unsigned int* d_ray_samples) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "render: unknown id %d", vol_id);
+    if (!h_cams || !out_rgba) return fail(ctx, VR_ERR_INVALID_ARG, "render: NULL pointer");
+    if (n_cams < 1 || W < 1 || H < 1 || W > 16384 || H > 16384)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: bad image size %d x %d x %d", n_cams, W, H);
+    if (!v->morph_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_precompute_morphology first");
+    if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_set_tissue_params first");
+    vr_render_opts o{VR_KERNEL_AUTO, 1, 8, 4};
+    if (opts) o = *opts;
+    if (o.kernel < 0 || o.kernel > 2) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
+    if (o.kernel == VR_KERNEL_STAGED) return fail(ctx, VR_ERR_INVALID_ARG, "render: staged kernel not built yet");
+    DeviceGuard g(ctx->device);
+    float* dst = out_rgba;
+    const size_t img_bytes = sizeof(float) * 4 * (size_t)n_cams * W * H;
+    if (out_on_host) {
+        CK(ensure_stage(ctx, img_bytes), "render: image staging buffer");
+        dst = (float*)ctx->d_stage;
+    }
+    RenderLaunch L;
+    memset(&L, 0, sizeof L);
+    L.vol.n[0] = v->n[0], L.vol.n[1] = v->n[1], L.vol.n[2] = v->n[2];
+    L.vol.nb[0] = v->nb[0], L.vol.nb[1] = v->nb[1], L.vol.nb[2] = v->nb[2];
+    L.vol.s[0] = v->s[0], L.vol.s[1] = v->s[1], L.vol.s[2] = v->s[2];
+    L.vol.bricks = v->d_bricks;
+    L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
+    L.vol.empty = v->d_empty;
+    L.vol.vc = v->d_vc;
+    L.tp = v->tp;
+    L.tf = v->d_tf;
+    L.out = dst;
+    L.counters = d_counters;
+    L.ray_samples = d_ray_samples;
+    L.W = W, L.H = H;
+    L.skip = o.skip_empty ? 1 : 0;
+    for (int c0 = 0; c0 < n_cams; c0 += kMaxCamsPerLaunch) {
+        const int nc = n_cams - c0 < kMaxCamsPerLaunch ? n_cams - c0 : kMaxCamsPerLaunch;
+        L.n_cams = nc;
+        L.cam_offset = c0;
+        memcpy(L.cams, h_cams + c0, sizeof(CamDev) * nc);
+        CK(launch_render_gather(L, ctx->stream), "render kernel");
+    }
+    if (out_on_host)
+        CK(cudaMemcpyAsync(out_rgba, dst, img_bytes, cudaMemcpyDeviceToHost, ctx->stream), "render: copy image back");
+    return VR_OK;
+}
+
+}  // extern "C"

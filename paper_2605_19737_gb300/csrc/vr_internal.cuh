@@ -1,0 +1,84 @@
+// vr_internal.cuh -- declarations shared by the library's translation units.
+//
+// Volume storage: the volume is cut into bricks of 8^3 interpolation cells
+// (cell i0 spans voxels i0 and i0+1 along each axis; a sample whose clamped
+// coordinate u_c has floor cell i0 = min(floor(u_c), N-2) belongs to brick
+// i0 / 8). Each brick is stored as a dense 12^3 float32 block holding voxels
+// [8b-1, 8b+11) per axis with clamp-to-edge values outside the volume: the
+// 4-tap stencils of a cell (voxels i0-1 .. i0+2) always fall inside it. The
+// block is 6912 bytes (a multiple of 16), so one bulk copy moves it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vr.h"
+
+namespace vr {
+
+constexpr int kCells = 8;                          // interpolation cells per brick edge
+constexpr int kEdge = 12;                          // stored brick edge (1 low + 8 + 3 high apron)
+constexpr int kBrickVox = kEdge * kEdge * kEdge;   // 1728 floats
+constexpr int kBrickBytes = kBrickVox * 4;         // 6912 bytes
+constexpr int kMaxCamsPerLaunch = 64;
+
+struct CamDev {
+    float eye[3], fwd[3], right[3], up[3];
+};
+
+struct TissueDev {
+    int tf_mode, tf_w, tf_h, grad_mod, shading;
+    float gamma, kappa_ref, w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox;
+};
+
+// Per-volume constants that kernels read from device memory (so that host code
+// never waits for the reductions that produce them).
+struct VolConst {
+    float imin, imax, range, gmax;
+};
+
+struct VolumeDev {
+    int n[3];       // voxels per axis
+    int nb[3];      // bricks per axis = ceil((n-1)/8)
+    float s[3];     // spacing (mm)
+    const float* bricks;     // nbricks * kBrickVox
+    const float* vbricks;    // vesselness bricks (same layout) or nullptr
+    const uint8_t* empty;    // nbricks flags, 1 = skip
+    const VolConst* vc;
+};
+
+struct RenderLaunch {
+    VolumeDev vol;
+    TissueDev tp;
+    const float* tf;           // [tf_h][tf_w][4]
+    float* out;                // [n_cams][H][W][4]
+    vr_counters* counters;     // nullable
+    unsigned* ray_samples;     // nullable, [n_cams][H][W][2]
+    int W, H, n_cams, cam_offset;
+    int skip;
+    int packet_w, packet_h;    // staged kernel packet shape (packet_w * packet_h == 32)
+    unsigned* work_counter;    // staged kernel work queue (zeroed before launch)
+    int n_packets_x, n_packets_y, n_work;
+    CamDev cams[kMaxCamsPerLaunch];
+};
+
+// ---------------------------------------------------------------- launchers
+// All return cudaSuccess or the launch error; all enqueue on `st`.
+cudaError_t launch_minmax_partials(const void* data, vr_dtype dt, long long n, float* partials, int nblocks,
+                                   cudaStream_t st);
+cudaError_t launch_minmax_final(const float* partials, int nblocks, float* out2, cudaStream_t st);
+int minmax_blocks(long long n);
+
+cudaError_t launch_normalize(const void* raw, vr_dtype dt, long long n, const float* minmax2, VolConst* vc,
+                             float* norm, cudaStream_t st);
+cudaError_t launch_make_bricks(const float* norm, const int n[3], const int nb[3], float* bricks, cudaStream_t st);
+cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* grid,
+                                cudaStream_t st);
+cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], VolConst* vc, cudaStream_t st);
+cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
+                            uint8_t* empty, int* prefix_scratch /* tf_w + 1 ints */, cudaStream_t st);
+
+cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
+cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, cudaStream_t st);
+
+}  // namespace vr

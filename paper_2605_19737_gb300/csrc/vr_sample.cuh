@@ -1,0 +1,271 @@
+// vr_sample.cuh -- per-ray and per-sample device math of the raymarch.
+//
+// Ray setup (pinhole camera, slab intersection, sample count) runs once per
+// ray in FP64 with explicit round-to-nearest operations; it yields each
+// sample's continuous voxel coordinate as a float32 head/tail pair so that the
+// per-sample position carries ~1e-5 voxel of error at any depth.
+//
+// The sample field is the trilinear interpolation of the voxel-wise intensity,
+// central-difference gradient (Eq. 2) and Hessian (Sec. 2.3). Along one axis,
+// with cell origin i0 and fraction f, these are 4-tap filters over voxels
+// i0-1 .. i0+2:
+//   value        w0 = [0, 1-f, f, 0]
+//   d/dx         w1 = [-(1-f), -f, 1-f, f] / 2          (divided by the spacing)
+//   d^2/dx^2     w2 = [1-f, 3f-2, 1-3f, f]              (divided by spacing^2)
+// and the 3D quantities are separable products of them (mixed second
+// derivatives use w1 on both axes). The contraction below reads the 56 voxels
+// of the 4x4x4 neighbourhood that carry weight (the 8 outer corners never
+// do), contracting x, then y, then z.
+#pragma once
+
+#include "vr_internal.cuh"
+
+namespace vr {
+
+struct RayDev {
+    int ns;           // number of samples t_k = t_near + (k+1/2) dt < t_far
+    float uhi[3];     // voxel coordinate at t_near: head
+    float ulo[3];     //                             tail
+    float dhi[3];     // voxel-coordinate step per sample: head
+    float dlo[3];     //                                   tail
+    float dir[3];     // unit ray direction
+};
+
+// Returns false when the ray misses the volume box or has no sample.
+__device__ __forceinline__ bool setup_ray(const CamDev& c, int W, int H, int i, int j, const int n[3],
+                                          const float s[3], float step_vox, RayDev& r) {
+    const double a = __dsub_rn(__ddiv_rn(__dmul_rn(2.0, (double)i + 0.5), (double)W), 1.0);
+    const double b = __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, (double)j + 0.5), (double)H));
+    double d[3], o[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        o[q] = (double)c.eye[q];
+        d[q] = __dadd_rn(__dadd_rn((double)c.fwd[q], __dmul_rn(a, (double)c.right[q])),
+                         __dmul_rn(b, (double)c.up[q]));
+    }
+    const double len =
+        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d[q] = __ddiv_rn(d[q], len);
+    double t0 = -INFINITY, t1 = INFINITY;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double hi = __dmul_rn((double)n[q], (double)s[q]);
+        if (d[q] == 0.0) {
+            if (o[q] < 0.0 || o[q] > hi) return false;
+            continue;
+        }
+        const double ta = __ddiv_rn(__dsub_rn(0.0, o[q]), d[q]);
+        const double tb = __ddiv_rn(__dsub_rn(hi, o[q]), d[q]);
+        const double lo_t = ta < tb ? ta : tb, hi_t = ta < tb ? tb : ta;
+        if (lo_t > t0) t0 = lo_t;
+        if (hi_t < t1) t1 = hi_t;
+    }
+    const double tn = t0 > 0.0 ? t0 : 0.0, tf = t1;
+    if (!(tn < tf)) return false;
+    const double dt = __dmul_rn((double)step_vox, (double)fminf(s[0], fminf(s[1], s[2])));
+    // ns = #{k >= 0 : t_near + (k + 1/2) dt < t_far}: estimate, then settle on the exact predicate.
+    long long ns = (long long)ceil(__dsub_rn(__ddiv_rn(__dsub_rn(tf, tn), dt), 0.5));
+    if (ns < 0) ns = 0;
+    while (ns > 0 && !(__dadd_rn(tn, __dmul_rn((double)(ns - 1) + 0.5, dt)) < tf)) --ns;
+    while (__dadd_rn(tn, __dmul_rn((double)ns + 0.5, dt)) < tf) ++ns;
+    if (ns == 0) return false;
+    r.ns = (int)ns;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double un = __dsub_rn(__ddiv_rn(__dadd_rn(o[q], __dmul_rn(tn, d[q])), (double)s[q]), 0.5);
+        r.uhi[q] = (float)un;
+        r.ulo[q] = (float)__dsub_rn(un, (double)r.uhi[q]);
+        const double st = __ddiv_rn(__dmul_rn(dt, d[q]), (double)s[q]);
+        r.dhi[q] = (float)st;
+        r.dlo[q] = (float)__dsub_rn(st, (double)r.dhi[q]);
+        r.dir[q] = (float)d[q];
+    }
+    return true;
+}
+
+// Continuous voxel coordinate of sample k along axis q.
+__device__ __forceinline__ float sample_u(const RayDev& r, int q, float kk) {
+    return fmaf(kk, r.dhi[q], r.uhi[q]) + fmaf(kk, r.dlo[q], r.ulo[q]);
+}
+
+// Clamp u to [0, n-1]; cell origin i0 = min(floor(u_c), n-2); fraction f = u_c - i0.
+__device__ __forceinline__ void cell_of(float u, int n, int& i0, float& f) {
+    const float uc = fminf(fmaxf(u, 0.0f), (float)(n - 1));
+    i0 = min((int)uc, n - 2);
+    f = uc - (float)i0;
+}
+
+// Sample field: out = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (not yet divided
+// by the spacing). `load(o)` returns the brick value at flat offset o; `base` is
+// the offset of tap (0,0,0) = voxel (i0-1, j0-1, k0-1).
+template <class Load>
+__device__ __forceinline__ void field_eval(const Load& load, int base, float fx, float fy, float fz, float out[10]) {
+    const float gxw = 1.0f - fx, gyw = 1.0f - fy, gzw = 1.0f - fz;
+    const float w1x[4] = {-0.5f * gxw, -0.5f * fx, 0.5f * gxw, 0.5f * fx};
+    const float w2x[4] = {gxw, fmaf(3.0f, fx, -2.0f), fmaf(-3.0f, fx, 1.0f), fx};
+    const float w0y[4] = {0.0f, gyw, fy, 0.0f};
+    const float w1y[4] = {-0.5f * gyw, -0.5f * fy, 0.5f * gyw, 0.5f * fy};
+    const float w2y[4] = {gyw, fmaf(3.0f, fy, -2.0f), fmaf(-3.0f, fy, 1.0f), fy};
+    const float w0z[4] = {0.0f, gzw, fz, 0.0f};
+    const float w1z[4] = {-0.5f * gzw, -0.5f * fz, 0.5f * gzw, 0.5f * fz};
+    const float w2z[4] = {gzw, fmaf(3.0f, fz, -2.0f), fmaf(-3.0f, fz, 1.0f), fz};
+    float I = 0.f, gx = 0.f, gy = 0.f, gz = 0.f, hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const bool zmid = (c == 1 || c == 2);
+        float A00 = 0.f, A10 = 0.f, A20 = 0.f, A01 = 0.f, A11 = 0.f, A02 = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const bool ymid = (b == 1 || b == 2);
+            const int ro = base + c * (kEdge * kEdge) + b * kEdge;
+            const float v1 = load(ro + 1), v2 = load(ro + 2);
+            const float X0 = fmaf(fx, v2, gxw * v1);
+            float X1 = 0.f, X2 = 0.f;
+            if (ymid || zmid) {
+                const float v0 = load(ro), v3 = load(ro + 3);
+                X1 = fmaf(w1x[3], v3, fmaf(w1x[2], v2, fmaf(w1x[1], v1, w1x[0] * v0)));
+                if (ymid && zmid) X2 = fmaf(w2x[3], v3, fmaf(w2x[2], v2, fmaf(w2x[1], v1, w2x[0] * v0)));
+            }
+            if (ymid) {
+                A00 = fmaf(w0y[b], X0, A00);
+                A10 = fmaf(w0y[b], X1, A10);
+                if (zmid) A20 = fmaf(w0y[b], X2, A20);
+            }
+            A01 = fmaf(w1y[b], X0, A01);
+            if (zmid) {
+                A11 = fmaf(w1y[b], X1, A11);
+                A02 = fmaf(w2y[b], X0, A02);
+            }
+        }
+        if (zmid) {
+            I = fmaf(w0z[c], A00, I);
+            gx = fmaf(w0z[c], A10, gx);
+            hxx = fmaf(w0z[c], A20, hxx);
+            gy = fmaf(w0z[c], A01, gy);
+            hxy = fmaf(w0z[c], A11, hxy);
+            hyy = fmaf(w0z[c], A02, hyy);
+        }
+        gz = fmaf(w1z[c], A00, gz);
+        hzz = fmaf(w2z[c], A00, hzz);
+        hxz = fmaf(w1z[c], A10, hxz);
+        hyz = fmaf(w1z[c], A01, hyz);
+    }
+    out[0] = I;
+    out[1] = gx;
+    out[2] = gy;
+    out[3] = gz;
+    out[4] = hxx;
+    out[5] = hyy;
+    out[6] = hzz;
+    out[7] = hxy;
+    out[8] = hxz;
+    out[9] = hyz;
+}
+
+// Trilinear value only (the vesselness channel): 8 corner voxels of the cell.
+template <class Load>
+__device__ __forceinline__ float value_eval(const Load& load, int base, float fx, float fy, float fz) {
+    const int o = base + kEdge * kEdge + kEdge + 1;  // tap (1,1,1) = voxel (i0, j0, k0)
+    const float c00 = fmaf(fx, load(o + 1), (1.f - fx) * load(o));
+    const float c10 = fmaf(fx, load(o + kEdge + 1), (1.f - fx) * load(o + kEdge));
+    const float c01 = fmaf(fx, load(o + kEdge * kEdge + 1), (1.f - fx) * load(o + kEdge * kEdge));
+    const float c11 = fmaf(fx, load(o + kEdge * kEdge + kEdge + 1), (1.f - fx) * load(o + kEdge * kEdge + kEdge));
+    const float c0 = fmaf(fy, c10, (1.f - fy) * c00);
+    const float c1 = fmaf(fy, c11, (1.f - fy) * c01);
+    return fmaf(fz, c1, (1.f - fz) * c0);
+}
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
+    return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), fmaf(t, b.z - a.z, a.z),
+                       fmaf(t, b.w - a.w, a.w));
+}
+
+// Piecewise-linear transfer function: x over tf_w entries, y over tf_h rows.
+__device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tf, int w, int h, float x, float y) {
+    const float xs = fminf(fmaxf(x, 0.0f), 1.0f) * (float)(w - 1);
+    const int j = min((int)xs, w - 2);
+    const float t = xs - (float)j;
+    if (h == 1) return lerp4(__ldg(tf + j), __ldg(tf + j + 1), t);
+    const float ys = fminf(fmaxf(y, 0.0f), 1.0f) * (float)(h - 1);
+    const int k = min((int)ys, h - 2);
+    const float q = ys - (float)k;
+    const float4* r0 = tf + (long long)k * w + j;
+    const float4 lo = lerp4(__ldg(r0), __ldg(r0 + 1), t);
+    const float4 hi = lerp4(__ldg(r0 + w), __ldg(r0 + w + 1), t);
+    return lerp4(lo, hi, q);
+}
+
+// Opacity (Eq. 4) and colour of one sample from its field (already scaled to
+// mm units) and vesselness value.
+__device__ __forceinline__ void sample_optics(const float f[10], float vval, const float dir[3], const TissueDev& tp,
+                                              const float4* __restrict__ tf, float inv_gmax, float& alpha,
+                                              float col[3]) {
+    const float gx = f[1], gy = f[2], gz = f[3];
+    const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
+    if (gg > 0.0f) {
+        gmag = sqrtf(gg);
+        const float Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
+        const float Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
+        const float Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
+        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) / gg;
+        const float inv = 1.0f / gmag;
+        hx = gx * inv;
+        hy = gy * inv;
+        hz = gz * inv;
+    }
+    const float gn = gmag * inv_gmax;
+    const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
+    const float4 c = tf_lookup(tf, tp.tf_w, tp.tf_h, f[0], y);
+    const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
+    const float wk = fminf(fmaxf(1.0f + tp.gamma * kappa / tp.kappa_ref, 0.0f), tp.w_max);
+    alpha = fminf(fmaxf(tp.opacity_scale * c.w * mg * wk, 0.0f), 1.0f);
+    if (tp.shading) {
+        const float d = fabsf(fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2])));
+        const float d2 = d * d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;
+        const float lit = fmaf(tp.kd, d, tp.ka);
+        const float spec = tp.ks * d16;
+        col[0] = fmaf(c.x, lit, spec);
+        col[1] = fmaf(c.y, lit, spec);
+        col[2] = fmaf(c.z, lit, spec);
+    } else {
+        col[0] = c.x;
+        col[1] = c.y;
+        col[2] = c.z;
+    }
+}
+
+// Divide the raw stencil sums by the spacing (gradient) and spacing products (Hessian).
+__device__ __forceinline__ void scale_field(float f[10], const float is[3]) {
+    f[1] *= is[0];
+    f[2] *= is[1];
+    f[3] *= is[2];
+    f[4] *= is[0] * is[0];
+    f[5] *= is[1] * is[1];
+    f[6] *= is[2] * is[2];
+    f[7] *= is[0] * is[1];
+    f[8] *= is[0] * is[2];
+    f[9] *= is[1] * is[2];
+}
+
+// First sample index >= k whose cell lies outside brick (b0, b1, b2), for a ray
+// currently in that brick; a lower bound (one sample earlier is re-tested by
+// the caller), never beyond ns.
+__device__ __forceinline__ int brick_exit_k(const RayDev& r, const int bcell[3], int k, int ns) {
+    float kmin = (float)ns;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float st = r.dhi[q];
+        if (st == 0.0f) continue;
+        const float bound = st > 0.0f ? (float)(kCells * (bcell[q] + 1)) : (float)(kCells * bcell[q]);
+        // u(k) = u_n + (k + 1/2) st crosses `bound` at k* = (bound - u_n)/st - 1/2
+        const float ks = (bound - r.uhi[q] - r.ulo[q]) / st - 0.5f;
+        kmin = fminf(kmin, st > 0.0f ? ceilf(ks) : floorf(ks) + 1.0f);
+    }
+    int ke = (int)fmaxf(kmin, 0.0f) - 1;  // back off one sample
+    if (ke <= k) ke = k + 1;
+    return min(ke, ns);
+}
+
+}  // namespace vr

@@ -1,0 +1,308 @@
+// vr_volume.cu -- per-volume stages: the parallel reductions of Eq. 1 and
+// Eq. 4 (Sec. 2.2, Sec. 4), min-max normalisation (Eq. 1), bricking with a
+// clamp-to-edge apron, the quantised per-brick min/max grid and the
+// transfer-function-driven empty-brick classification (the calvarium culling
+// by transfer-function clipping of Sec. 2.2, used for empty-space skipping).
+//
+// All of these are HBM-bound streaming kernels: coalesced x-fastest access,
+// 16-byte vector loads where the layout allows, grids sized in multiples of
+// the SM count.
+#include <math.h>
+
+#include "vr_internal.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr int kReduceThreads = 256;
+constexpr int kSMs = 152;
+
+__device__ __forceinline__ void warp_minmax(float& lo, float& hi) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+}
+
+// Block-wide min/max; result valid in thread 0.
+__device__ __forceinline__ void block_minmax(float& lo, float& hi) {
+    __shared__ float slo[32], shi[32];
+    warp_minmax(lo, hi);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        slo[w] = lo;
+        shi[w] = hi;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        lo = l < nw ? slo[l] : INFINITY;
+        hi = l < nw ? shi[l] : -INFINITY;
+        warp_minmax(lo, hi);
+    }
+}
+
+__device__ __forceinline__ void acc(float v, float& lo, float& hi) {
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+}
+
+// Per-block partial min/max over a grid-stride range; float32 input read as float4.
+__global__ void __launch_bounds__(kReduceThreads) k_minmax_partials_f32(const float* __restrict__ x, long long n,
+                                                                        float* __restrict__ partials) {
+    float lo = INFINITY, hi = -INFINITY;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    long long done = 0;
+    if (aligned) {
+        const long long n4 = n >> 2;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        for (long long i = tid; i < n4; i += stride) {
+            float4 v = __ldg(x4 + i);
+            acc(v.x, lo, hi);
+            acc(v.y, lo, hi);
+            acc(v.z, lo, hi);
+            acc(v.w, lo, hi);
+        }
+        done = n4 << 2;
+    }
+    for (long long i = done + tid; i < n; i += stride) acc(__ldg(x + i), lo, hi);
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = lo;
+        partials[2 * blockIdx.x + 1] = hi;
+    }
+}
+
+// uint16 input read as 8 values per 16-byte load.
+__global__ void __launch_bounds__(kReduceThreads) k_minmax_partials_u16(const uint16_t* __restrict__ x, long long n,
+                                                                        float* __restrict__ partials) {
+    float lo = INFINITY, hi = -INFINITY;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    long long done = 0;
+    if (aligned) {
+        const long long n8 = n >> 3;
+        const uint4* x8 = reinterpret_cast<const uint4*>(x);
+        for (long long i = tid; i < n8; i += stride) {
+            uint4 v = __ldg(x8 + i);
+            const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc((float)(w[q] & 0xffffu), lo, hi);
+                acc((float)(w[q] >> 16), lo, hi);
+            }
+        }
+        done = n8 << 3;
+    }
+    for (long long i = done + tid; i < n; i += stride) acc((float)__ldg(x + i), lo, hi);
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = lo;
+        partials[2 * blockIdx.x + 1] = hi;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_minmax_final(const float* __restrict__ partials, int nblocks,
+                                                       float* __restrict__ out2) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        lo = fminf(lo, partials[2 * i]);
+        hi = fmaxf(hi, partials[2 * i + 1]);
+    }
+    block_minmax(lo, hi);
+    if (threadIdx.x == 0) {
+        out2[0] = lo;
+        out2[1] = hi;
+    }
+}
+
+// Eq. 1 in float32, one IEEE round-to-nearest operation at a time:
+// d = x - I_min; I_norm = d / (I_max - I_min). Also publishes the constants.
+template <typename T>
+__global__ void k_normalize(const T* __restrict__ raw, long long n, const float* __restrict__ mm,
+                            VolConst* __restrict__ vc, float* __restrict__ out) {
+    const float imin = __ldg(mm), imax = __ldg(mm + 1);
+    const float range = __fsub_rn(imax, imin);
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        vc->imin = imin;
+        vc->imax = imax;
+        vc->range = range;
+    }
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = tid; i < n; i += stride) out[i] = __fdiv_rn(__fsub_rn((float)__ldg(raw + i), imin), range);
+}
+
+// One CTA per brick: copy voxels [8b-1, 8b+11) per axis (clamped) into the
+// brick's 12^3 block. Reads are row-contiguous in x, writes fully contiguous.
+__global__ void __launch_bounds__(256) k_make_bricks(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
+                                                     int nby, float* __restrict__ bricks) {
+    const long long b = blockIdx.x;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    float* dst = bricks + b * kBrickVox;
+    for (int e = threadIdx.x; e < kBrickVox; e += blockDim.x) {
+        const int lx = e % kEdge, ly = (e / kEdge) % kEdge, lz = e / (kEdge * kEdge);
+        const int x = min(max(kCells * bx - 1 + lx, 0), nx - 1);
+        const int y = min(max(kCells * by - 1 + ly, 0), ny - 1);
+        const int z = min(max(kCells * bz - 1 + lz, 0), nz - 1);
+        dst[e] = __ldg(norm + ((long long)z * ny + y) * nx + x);
+    }
+}
+
+// One warp per brick: min/max of I_norm over the brick's corner voxels
+// [8b, min(8b+8, N-1)] per axis, quantised to qlo = floor(min*65535),
+// qhi = ceil(max*65535) (float32 round-to-nearest products).
+__global__ void __launch_bounds__(256) k_brick_minmax(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
+                                                      int nby, long long nbricks, uint16_t* __restrict__ grid) {
+    const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nbricks) return;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    const int x0 = kCells * bx, y0 = kCells * by, z0 = kCells * bz;
+    const int ex = min(x0 + kCells, nx - 1) - x0 + 1;
+    const int ey = min(y0 + kCells, ny - 1) - y0 + 1;
+    const int ez = min(z0 + kCells, nz - 1) - z0 + 1;
+    float lo = INFINITY, hi = -INFINITY;
+    const int cnt = ex * ey * ez;
+    for (int e = lane; e < cnt; e += 32) {
+        const int lx = e % ex, ly = (e / ex) % ey, lz = e / (ex * ey);
+        acc(__ldg(norm + ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx)), lo, hi);
+    }
+    warp_minmax(lo, hi);
+    if (lane == 0) {
+        grid[2 * b] = (uint16_t)floorf(__fmul_rn(lo, 65535.0f));
+        grid[2 * b + 1] = (uint16_t)ceilf(__fmul_rn(hi, 65535.0f));
+    }
+}
+
+// |grad I|_max: largest voxel-wise central-difference gradient magnitude
+// (Eq. 2 with clamp-to-edge neighbours), reduced per block then combined with
+// an integer atomicMax on the (non-negative) float's bit pattern.
+__global__ void __launch_bounds__(256) k_gmax(const float* __restrict__ I, int nx, int ny, int nz, float hx, float hy,
+                                              float hz, VolConst* __restrict__ vc) {
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int k = blockIdx.z;
+    float m = 0.0f;
+    if (i < nx && j < ny) {
+        const long long row = (long long)ny * nx;
+        const float* c = I + (long long)k * row + (long long)j * nx + i;
+        const float gx = (__ldg(c + (i + 1 < nx ? 1 : 0)) - __ldg(c - (i > 0 ? 1 : 0))) * hx;
+        const float gy = (__ldg(c + (j + 1 < ny ? nx : 0)) - __ldg(c - (j > 0 ? nx : 0))) * hy;
+        const float gz = (__ldg(c + (k + 1 < nz ? row : 0)) - __ldg(c - (k > 0 ? row : 0))) * hz;
+        m = sqrtf(gx * gx + gy * gy + gz * gz);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float sm[8];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, sm[w]);
+        atomicMax(reinterpret_cast<int*>(&vc->gmax), __float_as_int(m));
+    }
+}
+
+// For every intensity column j of the transfer function: 1 if any row has a
+// non-zero opacity; then an exclusive prefix count, so that a brick's column
+// range can be tested in O(1). One block.
+__global__ void k_tf_alpha_prefix(const float* __restrict__ tf, int w, int h, int* __restrict__ prefix) {
+    __shared__ int col[4096];
+    for (int j = threadIdx.x; j < w; j += blockDim.x) {
+        int any = 0;
+        for (int r = 0; r < h && !any; ++r) any = tf[4 * ((long long)r * w + j) + 3] != 0.0f;
+        col[j] = any;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int j = 0; j < w; ++j) {
+            prefix[j] = run;
+            run += col[j];
+        }
+        prefix[w] = run;
+    }
+}
+
+// A brick is empty when no transfer-function column in
+// [floor(qlo*(w-1)/65535) - 1, ceil(qhi*(w-1)/65535) + 1] has any opacity.
+__global__ void k_classify(const uint16_t* __restrict__ grid, long long nbricks, const int* __restrict__ prefix,
+                           int w, uint8_t* __restrict__ empty) {
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbricks) return;
+    const long long ql = grid[2 * b], qh = grid[2 * b + 1];
+    long long jl = (ql * (w - 1)) / 65535 - 1;
+    long long jh = (qh * (w - 1) + 65534) / 65535 + 1;
+    if (jl < 0) jl = 0;
+    if (jh > w - 1) jh = w - 1;
+    empty[b] = (uint8_t)(prefix[jh + 1] - prefix[jl] == 0);
+}
+
+}  // namespace
+
+int minmax_blocks(long long n) {
+    long long want = (n + (long long)kReduceThreads * 16 - 1) / ((long long)kReduceThreads * 16);
+    if (want < 1) want = 1;
+    if (want > kSMs * 8) want = kSMs * 8;
+    return (int)want;
+}
+
+cudaError_t launch_minmax_partials(const void* data, vr_dtype dt, long long n, float* partials, int nblocks,
+                                   cudaStream_t st) {
+    if (dt == VR_F32)
+        k_minmax_partials_f32<<<nblocks, kReduceThreads, 0, st>>>((const float*)data, n, partials);
+    else
+        k_minmax_partials_u16<<<nblocks, kReduceThreads, 0, st>>>((const uint16_t*)data, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minmax_final(const float* partials, int nblocks, float* out2, cudaStream_t st) {
+    k_minmax_final<<<1, 1024, 0, st>>>(partials, nblocks, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(const void* raw, vr_dtype dt, long long n, const float* minmax2, VolConst* vc,
+                             float* norm, cudaStream_t st) {
+    const int blocks = kSMs * 8;
+    if (dt == VR_F32)
+        k_normalize<float><<<blocks, 256, 0, st>>>((const float*)raw, n, minmax2, vc, norm);
+    else
+        k_normalize<uint16_t><<<blocks, 256, 0, st>>>((const uint16_t*)raw, n, minmax2, vc, norm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_bricks(const float* norm, const int n[3], const int nb[3], float* bricks, cudaStream_t st) {
+    const long long nbr = (long long)nb[0] * nb[1] * nb[2];
+    k_make_bricks<<<(unsigned)nbr, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], bricks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* grid,
+                                cudaStream_t st) {
+    const long long nbr = (long long)nb[0] * nb[1] * nb[2];
+    const unsigned blocks = (unsigned)((nbr + 7) / 8);
+    k_brick_minmax<<<blocks, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], nbr, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], VolConst* vc, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&vc->gmax, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    dim3 grid((n[0] + 31) / 32, (n[1] + 7) / 8, n[2]);
+    k_gmax<<<grid, 256, 0, st>>>(norm, n[0], n[1], n[2], 0.5f / s[0], 0.5f / s[1], 0.5f / s[2], vc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
+                            uint8_t* empty, int* prefix_scratch, cudaStream_t st) {
+    k_tf_alpha_prefix<<<1, 256, 0, st>>>(tf, tf_w, tf_h, prefix_scratch);
+    k_classify<<<(unsigned)((nbricks + 255) / 256), 256, 0, st>>>(grid, nbricks, prefix_scratch, tf_w, empty);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

@@ -1,0 +1,236 @@
+"""GPU parity of the load / morphology / classification stages and the forward raymarch.
+
+Every check goes through the C ABI (libvr.so via the ctypes binding) and
+compares against the FP64 oracle on the same seeded inputs: bit-exact for the
+reductions' extrema, the quantised brick grid and the skip flags; within
+1e-4 max |dRGBA| for images; exact per-ray sample counts on unambiguous rays.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as ph
+from phantoms import workloads
+from tests.gpu_util import assert_counts, assert_rgba_parity, oracle_render_case, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+@pytest.fixture(scope="module")
+def vr(torch):
+    import paper_2605_19737_gb300 as pkg
+    ctx = pkg.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def _load_case(vr, torch, case, on_device=True):
+    vol = case["volume"]
+    data = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol)
+    if on_device:
+        data = data.cuda()
+    vid = vr.load_volume(data, case["spacing"])
+    vr.precompute_morphology(vid, case.get("sigmas", ()))
+    vr.set_tissue_params(vid, case["tf"], **case["params"])
+    return vid
+
+
+def _render(vr, torch, vid, case, **kw):
+    n = case["cams"].shape[0]
+    rs = torch.zeros((n, case["H"], case["W"], 2), dtype=torch.int32, device="cuda")
+    img = vr.render(vid, case["cams"], case["W"], case["H"], ray_samples=rs, **kw)
+    torch.cuda.synchronize()
+    return img.cpu().numpy(), rs.cpu().numpy().astype(np.int64)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint16])
+@pytest.mark.parametrize("n", [1, 7, 1000, 123457])
+def test_reduce_minmax_exact(vr, torch, dtype, n):
+    rng = np.random.default_rng(n)
+    x = (rng.normal(0, 100, n).astype(np.float32) if dtype == np.float32
+         else rng.integers(0, 4096, n).astype(np.uint16))
+    t = torch.from_numpy(x.view(np.int16) if dtype == np.uint16 else x).cuda()
+    out = vr.reduce_minmax(t).cpu().numpy()
+    assert out[0] == np.float32(x.min()) and out[1] == np.float32(x.max())
+
+
+@pytest.mark.parametrize("dims,dtype", [((19, 17, 10), np.float32), ((33, 9, 41), np.uint16),
+                                        ((64, 64, 64), np.float32)])
+def test_normalise_grid_and_gmax(vr, torch, dims, dtype):
+    vol = ph.random_volume(dims, 31, dtype, smooth=1)
+    vid = vr.load_volume(torch.from_numpy(vol.view(np.int16) if dtype == np.uint16 else vol).cuda())
+    vr.precompute_morphology(vid)
+    imin, imax, gmax = vr.get_norm(vid)
+    v32 = vol.astype(np.float32)
+    assert imin == v32.min() and imax == v32.max()
+    norm = vr.get_normalized(vid).cpu().numpy()
+    want32 = (v32 - np.float32(imin)) / np.float32(np.float32(imax) - np.float32(imin))
+    np.testing.assert_array_equal(norm, want32)  # same float32 operations: bit-exact
+    np.testing.assert_allclose(norm, oracle.normalize(vol), atol=2e-7)
+    grid, _ = vr.get_bricks(vid)
+    np.testing.assert_array_equal(grid, oracle.brick_minmax_q(vol))
+    assert gmax == pytest.approx(oracle.gmax(oracle.normalize(vol), (1, 1, 1)), rel=2e-6)
+    vr.free_volume(vid)
+
+
+def test_classification_bit_exact(vr, torch):
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    for tf in (case["tf"], ph.tf_2d_gradient(case["tf"]), ph.tf_constant((1, 1, 1), 0.0)):
+        mode = 0 if tf.shape[0] == 1 else 1
+        vr.set_tissue_params(vid, tf, **dict(case["params"], tf_mode=mode))
+        grid, empty = vr.get_bricks(vid)
+        np.testing.assert_array_equal(empty, oracle.classify(grid, tf))
+    vr.free_volume(vid)
+
+
+def test_head64_parity_and_counts(vr, torch):
+    """The head phantom workload (64^3 float32, 128x128, 1D TF, Phong, ET 0.99)."""
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    img, rs = _render(vr, torch, vid, case)
+    _, empty = vr.get_bricks(vid)
+    res = oracle_render_case(case, brick_empty=empty)
+    err, nflag = assert_rgba_parity(img, res, what="head64")
+    assert res.rgba[..., 3].max() > 0.5
+    assert_counts(rs, res)
+    print("head64: max|d| %.2e, flagged %d" % (err, nflag))
+    vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("kappa", [False, True])
+def test_brainweb_small_mode1_parity(vr, torch, kappa):
+    """uint16 BrainWeb-shaped volume, 2D gradient TF, curvature-modulated opacity,
+    3 cameras, ragged 100x75 image (several tiles plus partial ones)."""
+    case = workloads.scaled_brainweb((61, 73, 59), width=100, height=75, n_cams=3)
+    if not kappa:
+        case["params"] = dict(case["params"], gamma=0.0)
+    vid = _load_case(vr, torch, case)
+    img, rs = _render(vr, torch, vid, case)
+    _, empty = vr.get_bricks(vid)
+    res = oracle_render_case(case, brick_empty=empty)
+    assert_rgba_parity(img, res, what="brainweb small")
+    assert_counts(rs, res)
+    vr.free_volume(vid)
+
+
+def test_anisotropic_spacing_grad_mod(vr, torch):
+    rng = np.random.default_rng(41)
+    dims, sp = (30, 26, 22), (0.8, 1.1, 1.4)
+    vol = ph.head_phantom(dims, seed=41)
+    tf = ph.tf_1d_windows(ph.HEAD_WINDOWS, {"csf": 0.1, "gm": 0.2, "wm": 0.3}, ramp=0.05)
+    cams = ph.camera_array([ph.orbit_camera(dims, sp, rng.uniform(0, 360), rng.uniform(-60, 60), width=40,
+                                            height=33) for _ in range(2)])
+    params = workloads._params(tf_mode=0, grad_mod=1, shading=1, gamma=0.4, kappa_ref=0.1, w_max=2.5,
+                               et_threshold=0.95, step_vox=0.37)
+    case = dict(volume=vol, spacing=sp, cams=cams, W=40, H=33, tf=tf, params=params)
+    vid = _load_case(vr, torch, case)
+    img, rs = _render(vr, torch, vid, case)
+    _, empty = vr.get_bricks(vid)
+    res = oracle_render_case(case, brick_empty=empty)
+    assert_rgba_parity(img, res, what="anisotropic")
+    assert_counts(rs, res)
+    vr.free_volume(vid)
+
+
+def test_skip_is_bit_neutral_and_deterministic(vr, torch):
+    case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
+    vid = _load_case(vr, torch, case)
+    a, ra = _render(vr, torch, vid, case, skip_empty=True)
+    b, rb = _render(vr, torch, vid, case, skip_empty=False)
+    c, _ = _render(vr, torch, vid, case, skip_empty=True)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(ra[..., 0], rb[..., 0])
+    assert ra[..., 1].sum() < rb[..., 1].sum()  # skipping evaluated fewer samples
+    vr.free_volume(vid)
+
+
+def test_zero_opacity_and_host_output(vr, torch):
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    dev = vr.render(vid, case["cams"], 128, 128)
+    host = torch.empty((1, 128, 128, 4), dtype=torch.float32).pin_memory()
+    vr.render(vid, case["cams"], 128, 128, out=host)
+    vr.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), host.numpy())
+    vr.set_tissue_params(vid, ph.tf_constant((1, 1, 1), 0.0), **case["params"])
+    z = vr.render(vid, case["cams"], 128, 128)
+    assert float(z.abs().max()) == 0.0
+    vr.free_volume(vid)
+
+
+def test_counters_match_ray_samples(vr, torch):
+    import paper_2605_19737_gb300 as pkg
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    ctr = pkg.new_counters()
+    rs = torch.zeros((1, 128, 128, 2), dtype=torch.int32, device="cuda")
+    vr.render(vid, case["cams"], 128, 128, counters=ctr, ray_samples=rs)
+    c = ctr.cpu().numpy()
+    r = rs.cpu().numpy().astype(np.int64)
+    assert c[1] == r[..., 0].sum() and c[2] == r[..., 1].sum()
+    assert c[0] == int((r[..., 0] > 0).sum())
+    vr.free_volume(vid)
+
+
+def test_affine_intensity_invariance_gpu(vr, torch):
+    """Eq. 1 scanner agnosticism on the device: a*I + b renders the same image."""
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    a = vr.render(vid, case["cams"], 128, 128).cpu().numpy()
+    case2 = dict(case, volume=(case["volume"] * np.float32(3.0) + np.float32(250.0)).astype(np.float32))
+    vid2 = _load_case(vr, torch, case2)
+    b = vr.render(vid2, case["cams"], 128, 128).cpu().numpy()
+    np.testing.assert_allclose(a, b, atol=2e-5)
+    vr.free_volume(vid)
+    vr.free_volume(vid2)
+
+
+def test_error_paths(vr, torch):
+    import paper_2605_19737_gb300 as pkg
+    flat = torch.zeros((4, 4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(pkg.VRError) as e:
+        vr.load_volume(flat)
+    assert e.value.status == pkg.vr.VR_ERR_DEGENERATE
+    with pytest.raises(pkg.VRError) as e:
+        vr.load_volume(torch.zeros((4, 4, 1), dtype=torch.float32, device="cuda"))
+    assert e.value.status == pkg.vr.VR_ERR_INVALID_ARG
+    vol = torch.rand((8, 8, 8), device="cuda")
+    vid = vr.load_volume(vol)
+    cam = ph.orbit_camera((8, 8, 8), (1, 1, 1), 0, 0, width=4, height=4)
+    with pytest.raises(pkg.VRError) as e:
+        vr.render(vid, cam, 4, 4)
+    assert e.value.status == pkg.vr.VR_ERR_NOT_READY
+    with pytest.raises(pkg.VRError) as e:
+        vr.load_volume(vol, spacing=(1.0, -1.0, 1.0))
+    assert e.value.status == pkg.vr.VR_ERR_INVALID_ARG
+    vr.precompute_morphology(vid)
+    with pytest.raises(pkg.VRError) as e:
+        vr.set_tissue_params(vid, ph.tf_constant((1, 1, 1), 0.1), kappa_ref=0.0)
+    assert e.value.status == pkg.vr.VR_ERR_INVALID_ARG
+    vr.free_volume(vid)
+
+
+@pytest.mark.slow
+def test_brainweb_1080p_sampled_parity(vr, torch):
+    """Full-size workload (181x217x181 uint16, 1920x1080) in the benchmark's launch
+    configuration, checked on every 16th row and column against the oracle."""
+    case = workloads.brainweb_1080p()
+    vid = _load_case(vr, torch, case)
+    img, rs = _render(vr, torch, vid, case)
+    _, empty = vr.get_bricks(vid)
+    res = oracle_render_case(case, brick_empty=empty, pix_stride=16)
+    mask = np.zeros(img.shape[:3], bool)
+    mask[:, ::16, ::16] = True
+    err, nflag = assert_rgba_parity(img, res, mask=mask, what="brainweb 1080p")
+    assert_counts(rs, res, mask=mask)
+    assert res.rgba[mask][..., 3].max() > 0.5
+    print("brainweb_1080p sampled: max|d| %.2e flagged %d" % (err, nflag))
+    vr.free_volume(vid)
