@@ -176,8 +176,10 @@ def run(args):
     rays, dense, evald = [int(x) for x in ctr.cpu().numpy()[:3]]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    kernel = pkg.VR_KERNEL_STAGED if args.kernel == "staged" else pkg.VR_KERNEL_GATHER
+
     def frame():
-        ctx.render(vid, case["cams"], W, H, out=out)
+        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -216,7 +218,7 @@ def run(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ctx.set_tissue_params(vid, tf_host, **case["params"])
-        ctx.render(vid, case["cams"], W, H, out=img_host)
+        ctx.render(vid, case["cams"], W, H, out=img_host, kernel=kernel)
         ctx.synchronize()
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t1)
@@ -244,7 +246,7 @@ def run(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "brainweb_1080p", "volume": "181x217x181 u16 (BrainWeb-shaped phantom)",
                        "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows",
-                       "step_vox": 0.5, "kernel": "gather", "l2": "flushed between frames (256 MB write)",
+                       "step_vox": 0.5, "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fps": 1000.0 / ms,
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
@@ -275,6 +277,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="staged", choices=["staged", "gather"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -10,6 +10,7 @@
 #include <map>
 #include <string>
 
+#include "vr_async.cuh"
 #include "vr_internal.cuh"
 
 using namespace vr;
@@ -49,7 +50,8 @@ struct vr_ctx {
     int partials_cap = 0;
     void* d_stage = nullptr;
     size_t stage_cap = 0;
-    unsigned* d_work = nullptr;
+    unsigned* d_work = nullptr;   // [0]: staged-kernel work counter, [1]: status word
+    int staged_ctas[2][17] = {};   // resident CTAs per SM by (vesselness, warps per block)
 };
 
 namespace {
@@ -154,6 +156,7 @@ vr_status vr_create(vr_ctx** out, int device, void* cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     DeviceGuard g(device);
     cudaError_t e = cudaMalloc(&ctx->d_work, 64 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_work, 0, 64 * sizeof(unsigned));
     if (e != cudaSuccess) {
         delete ctx;
         (void)cudaGetLastError();
@@ -187,6 +190,13 @@ vr_status vr_synchronize(vr_ctx* ctx) {
     DeviceGuard g(ctx->device);
     CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
     CK(cudaGetLastError(), "asynchronous error");
+    unsigned status = 0;
+    CK(cudaMemcpy(&status, ctx->d_work + 1, sizeof status, cudaMemcpyDeviceToHost), "status word");
+    if (status) {
+        CK(cudaMemset(ctx->d_work + 1, 0, sizeof status), "status word reset");
+        if (status & kStatusTimeout)
+            return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait expired (bulk copy did not complete)");
+    }
     return VR_OK;
 }
 
@@ -452,7 +462,11 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     vr_render_opts o{VR_KERNEL_AUTO, 1, 8, 4};
     if (opts) o = *opts;
     if (o.kernel < 0 || o.kernel > 2) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
-    if (o.kernel == VR_KERNEL_STAGED) return fail(ctx, VR_ERR_INVALID_ARG, "render: staged kernel not built yet");
+    const bool staged = o.kernel != VR_KERNEL_GATHER;
+    if (staged && (o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16 && o.packet_w != 32))
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8, 16 or 32");
+    if (staged && (o.warps_per_block < 1 || o.warps_per_block > 8))
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be in [1, 8]");
     DeviceGuard g(ctx->device);
     float* dst = out_rgba;
     const size_t img_bytes = sizeof(float) * 4 * (size_t)n_cams * W * H;
@@ -476,12 +490,35 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.ray_samples = d_ray_samples;
     L.W = W, L.H = H;
     L.skip = o.skip_empty ? 1 : 0;
+    L.packet_w = o.packet_w;
+    L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
+    L.work_counter = ctx->d_work;
+    L.status = ctx->d_work + 1;
+    L.n_packets_x = (W + L.packet_w - 1) / L.packet_w;
+    L.n_packets_y = (H + L.packet_h - 1) / L.packet_h;
+    int ctas = 0;
+    if (staged) {
+        const bool ves = L.vol.vbricks != nullptr;
+        int& per_sm = ctx->staged_ctas[ves][o.warps_per_block];
+        if (per_sm == 0) CK(staged_config(o.warps_per_block, ves, &per_sm), "render: staged kernel configuration");
+        if (per_sm < 1) return fail(ctx, VR_ERR_INVALID_ARG, "render: staged kernel does not fit on an SM");
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "render: SM count");
+        ctas = sms * per_sm;
+    }
     for (int c0 = 0; c0 < n_cams; c0 += kMaxCamsPerLaunch) {
         const int nc = n_cams - c0 < kMaxCamsPerLaunch ? n_cams - c0 : kMaxCamsPerLaunch;
         L.n_cams = nc;
         L.cam_offset = c0;
         memcpy(L.cams, h_cams + c0, sizeof(CamDev) * nc);
-        CK(launch_render_gather(L, ctx->stream), "render kernel");
+        if (staged) {
+            L.n_work = nc * L.n_packets_x * L.n_packets_y;
+            const int need = (L.n_work + o.warps_per_block - 1) / o.warps_per_block;
+            CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), ctx->stream), "render: reset work counter");
+            CK(launch_render_staged(L, o.warps_per_block, ctas < need ? ctas : need, ctx->stream), "render kernel");
+        } else {
+            CK(launch_render_gather(L, ctx->stream), "render kernel");
+        }
     }
     if (out_on_host)
         CK(cudaMemcpyAsync(out_rgba, dst, img_bytes, cudaMemcpyDeviceToHost, ctx->stream), "render: copy image back");

@@ -58,6 +58,7 @@ struct RenderLaunch {
     int skip;
     int packet_w, packet_h;    // staged kernel packet shape (packet_w * packet_h == 32)
     unsigned* work_counter;    // staged kernel work queue (zeroed before launch)
+    unsigned* status;          // device status word (kStatusTimeout on an expired wait)
     int n_packets_x, n_packets_y, n_work;
     CamDev cams[kMaxCamsPerLaunch];
 };
@@ -79,6 +80,9 @@ cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float
                             uint8_t* empty, int* prefix_scratch /* tf_w + 1 ints */, cudaStream_t st);
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
-cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, cudaStream_t st);
+cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
+int staged_smem_bytes(int warps_per_block, bool vessel);
+// Set the kernel's dynamic shared-memory limit and report resident CTAs per SM.
+cudaError_t staged_config(int warps_per_block, bool vessel, int* ctas_per_sm);
 
 }  // namespace vr

@@ -6,6 +6,7 @@
 // from the bricked volume (L1/L2-resident), evaluates the field, Eq. 4 and the
 // shading, and composites by Eqs. 5-6. Samples in bricks classified empty are
 // skipped a brick at a time (bit-neutral: their opacity is exactly zero).
+#include "vr_async.cuh"
 #include "vr_sample.cuh"
 
 namespace vr {
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
             float f[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                cell_of(sample_u(r, q, kk), v.n[q], i0[q], f[q]);
+                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
                 bc[q] = i0[q] >> 3;
             }
             const long long bi = brick_index(v, bc);
@@ -107,6 +108,206 @@ cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st) {
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
     k_render_gather<<<grid, 128, 0, st>>>(L);
     return cudaGetLastError();
+}
+
+}  // namespace vr
+
+// ---------------------------------------------------------------------------
+// k_render_staged: persistent warps pull 32-ray packets (packet_w x packet_h
+// pixels) from an atomic work counter. A warp keeps one 12^3 brick (and, for
+// the vesselness transfer function, its V brick) in shared memory. Each round
+// every live lane skips empty bricks up to its next sample, the warp picks the
+// front-most brick any live lane needs (smallest per-axis brick distance from
+// the eye, a visibility order of the brick grid), one lane pulls it in with a
+// bulk copy completing on an mbarrier, and all lanes whose next sample lies in
+// that brick march through it from shared memory. Each lane still walks its own
+// samples strictly front to back, so the result equals the gather kernel's
+// bit for bit; the brick order only decides how often a brick is re-staged.
+namespace vr {
+namespace {
+
+struct SmemLoad {
+    const float* p;
+    __device__ __forceinline__ float operator()(int o) const { return p[o]; }
+};
+
+__device__ __forceinline__ unsigned brick_key(const int b[3], const int e[3]) {
+    const unsigned dx = min(abs(b[0] - e[0]), 1023), dy = min(abs(b[1] - e[1]), 1023), dz = min(abs(b[2] - e[2]), 1023);
+    return (dz << 20) | (dy << 10) | dx;
+}
+
+__global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ RenderLaunch L) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nchan = L.vol.vbricks ? 2 : 1;
+    const int per_warp = nchan * kBrickBytes + 128;
+    unsigned char* my = smem_raw + (size_t)warp * per_warp;
+    float* sbrick = reinterpret_cast<float*>(my);
+    float* svbrick = reinterpret_cast<float*>(my + kBrickBytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(my + nchan * kBrickBytes);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    unsigned parity = 0;
+    bool failed = false;
+
+    const VolumeDev& v = L.vol;
+    const float4* tf = reinterpret_cast<const float4*>(L.tf);
+    const float gmax = __ldg(&v.vc->gmax);
+    const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+    const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
+    const int ppx = L.packet_w, ppy = L.packet_h;
+    unsigned staged = 0, rays_hit = 0, dense_tot = 0, eval_tot = 0;
+
+    while (!failed) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(L.work_counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned)L.n_work) break;
+        const int px = item % L.n_packets_x;
+        const int py = (item / L.n_packets_x) % L.n_packets_y;
+        const int cam = item / (L.n_packets_x * L.n_packets_y);
+        const int i = px * ppx + lane % ppx, j = py * ppy + lane / ppx;
+        const bool inside = i < L.W && j < L.H;
+        const CamDev& cd = L.cams[cam];
+        int eb[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) eb[q] = (int)floorf((cd.eye[q] / v.s[q] - 0.5f) / (float)kCells);
+
+        RayDev r;
+        bool live = inside && setup_ray(cd, L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+        const bool hit = live;
+        int k = 0, kstop = -1, cur = -1, bc[3] = {0, 0, 0};
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+        unsigned evald = 0;
+
+        while (true) {
+            // skip empty bricks up to this lane's next evaluated sample
+            while (live && cur < 0) {
+                if (k >= r.ns) {
+                    live = false;
+                    break;
+                }
+                const float kk = (float)k + 0.5f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    int i0;
+                    float f;
+                    sample_cell(r, q, kk, v.n[q], i0, f);
+                    bc[q] = i0 >> 3;
+                }
+                const int bi = (int)brick_index(v, bc);
+                if (L.skip && __ldg(v.empty + bi)) {
+                    k = brick_exit_k(r, bc, k, r.ns);
+                } else {
+                    cur = bi;
+                }
+            }
+            const unsigned key = live ? brick_key(bc, eb) : 0xffffffffu;
+            const unsigned mk = __reduce_min_sync(0xffffffffu, key);
+            if (mk == 0xffffffffu) break;
+            const int leader = __ffs(__ballot_sync(0xffffffffu, key == mk)) - 1;
+            const int sel = __shfl_sync(0xffffffffu, cur, leader);
+            int sc[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sc[q] = __shfl_sync(0xffffffffu, bc[q], leader);
+
+            // stage brick `sel` (all lanes are done reading the previous one)
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, nchan * kBrickBytes);
+                bulk_g2s(sbrick, v.bricks + (size_t)sel * kBrickVox, kBrickBytes, bar);
+                if (nchan == 2) bulk_g2s(svbrick, v.vbricks + (size_t)sel * kBrickVox, kBrickBytes, bar);
+                ++staged;
+            }
+            const bool arrived = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+            if (!arrived) {
+                // the copy did not land within the budget: record it, give the copy one
+                // more bounded wait so nothing is in flight when the warp leaves, stop.
+                (void)mbar_wait_bounded(bar, parity);
+                failed = true;
+                if (lane == 0) atomicOr(L.status, kStatusTimeout);
+                break;
+            }
+            parity ^= 1u;
+
+            if (live && cur == sel) {
+                while (true) {
+                    const float kk = (float)k + 0.5f;
+                    int i0[3], b2[3];
+                    float f[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                        b2[q] = i0[q] >> 3;
+                    }
+                    if (b2[0] != sc[0] || b2[1] != sc[1] || b2[2] != sc[2]) {
+                        cur = -1;
+                        break;
+                    }
+                    const int base = ((i0[2] - kCells * sc[2]) * kEdge + (i0[1] - kCells * sc[1])) * kEdge +
+                                     (i0[0] - kCells * sc[0]);
+                    float fld[10];
+                    field_eval(SmemLoad{sbrick}, base, f[0], f[1], f[2], fld);
+                    scale_field(fld, is);
+                    const float vval = nchan == 2 ? value_eval(SmemLoad{svbrick}, base, f[0], f[1], f[2]) : 0.0f;
+                    float alpha, col[3];
+                    sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                    const float wgt = (1.0f - A) * alpha;  // Eqs. 5-6
+                    C0 = fmaf(col[0], wgt, C0);
+                    C1 = fmaf(col[1], wgt, C1);
+                    C2 = fmaf(col[2], wgt, C2);
+                    A += wgt;
+                    ++evald;
+                    if (A >= L.tp.et_threshold) {
+                        kstop = k;
+                        live = false;
+                        break;
+                    }
+                    if (++k >= r.ns) {
+                        live = false;
+                        break;
+                    }
+                }
+            }
+        }
+        if (failed) break;
+        const unsigned dense = hit ? (kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns) : 0u;
+        if (inside) {
+            const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
+            reinterpret_cast<float4*>(L.out)[pix] = make_float4(C0, C1, C2, A);
+            if (L.ray_samples) {
+                L.ray_samples[2 * pix] = dense;
+                L.ray_samples[2 * pix + 1] = evald;
+            }
+        }
+        rays_hit += hit ? 1u : 0u;
+        dense_tot += dense;
+        eval_tot += evald;
+    }
+    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u);
+}
+
+}  // namespace
+
+int staged_smem_bytes(int warps_per_block, bool vessel) {
+    return warps_per_block * ((vessel ? 2 : 1) * kBrickBytes + 128);
+}
+
+cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st) {
+    const int smem = staged_smem_bytes(warps_per_block, L.vol.vbricks != nullptr);
+    k_render_staged<<<ctas, warps_per_block * 32, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t staged_config(int warps_per_block, bool vessel, int* ctas_per_sm) {
+    const int smem = staged_smem_bytes(warps_per_block, vessel);
+    cudaError_t e = cudaFuncSetAttribute(k_render_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_render_staged, warps_per_block * 32, smem);
 }
 
 }  // namespace vr

@@ -1,9 +1,9 @@
 // vr_sample.cuh -- per-ray and per-sample device math of the raymarch.
 //
 // Ray setup (pinhole camera, slab intersection, sample count) runs once per
-// ray in FP64 with explicit round-to-nearest operations; it yields each
-// sample's continuous voxel coordinate as a float32 head/tail pair so that the
-// per-sample position carries ~1e-5 voxel of error at any depth.
+// ray in FP64 with explicit round-to-nearest operations; it yields the entry
+// point and per-sample step in voxel coordinates as float32 head/tail pairs,
+// from which each sample's cell fraction is formed to ~3e-8 at any depth.
 //
 // The sample field is the trilinear interpolation of the voxel-wise intensity,
 // central-difference gradient (Eq. 2) and Hessian (Sec. 2.3). Along one axis,
@@ -84,16 +84,36 @@ __device__ __forceinline__ bool setup_ray(const CamDev& c, int W, int H, int i, 
     return true;
 }
 
-// Continuous voxel coordinate of sample k along axis q.
+// Continuous voxel coordinate of sample k along axis q (head + tail rounded to
+// one float; used where a rounding-level error only moves a brick decision).
 __device__ __forceinline__ float sample_u(const RayDev& r, int q, float kk) {
     return fmaf(kk, r.dhi[q], r.uhi[q]) + fmaf(kk, r.dlo[q], r.ulo[q]);
 }
 
-// Clamp u to [0, n-1]; cell origin i0 = min(floor(u_c), n-2); fraction f = u_c - i0.
-__device__ __forceinline__ void cell_of(float u, int n, int& i0, float& f) {
-    const float uc = fminf(fmaxf(u, 0.0f), (float)(n - 1));
-    i0 = min((int)uc, n - 2);
-    f = uc - (float)i0;
+// Cell of sample k along axis q: u_c = clamp(u, 0, n-1), i0 = min(floor(u_c), n-2),
+// f = u_c - i0. u = u_n + (k + 1/2) step is carried as a double-float (exact
+// product by FMA, exact sum by TwoSum) so that f is accurate to ~3e-8 at any
+// depth; a single-float u would carry ~1e-5 voxel, which moves steep
+// transfer-function edges by more than the 1e-4 RGBA budget. Intrinsics keep
+// the compiler from contracting the error-free transformations.
+__device__ __forceinline__ void sample_cell(const RayDev& r, int q, float kk, int n, int& i0, float& f) {
+    const float ph = __fmul_rn(kk, r.dhi[q]);
+    const float pl = fmaf(kk, r.dhi[q], -ph);
+    const float s = __fadd_rn(r.uhi[q], ph);
+    const float bb = __fsub_rn(s, r.uhi[q]);
+    const float e = __fadd_rn(__fsub_rn(r.uhi[q], __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+    const float t = __fadd_rn(__fadd_rn(e, pl), fmaf(kk, r.dlo[q], r.ulo[q]));
+    const float u = __fadd_rn(s, t);
+    if (u <= 0.0f) {
+        i0 = 0;
+        f = 0.0f;
+    } else if (u >= (float)(n - 1)) {
+        i0 = n - 2;
+        f = 1.0f;
+    } else {
+        i0 = min((int)u, n - 2);
+        f = fminf(fmaxf(__fadd_rn(__fsub_rn(s, (float)i0), t), 0.0f), 1.0f);
+    }
 }
 
 // Sample field: out = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (not yet divided

@@ -1,0 +1,59 @@
+"""Render a named workload a few times (for Nsight Compute captures and quick timing).
+
+    python -m paper_2605_19737_gb300.profile_run --workload brainweb_1080p --kernel staged --frames 3
+
+Workloads: brainweb_1080p (181x217x181 uint16, 1920x1080), brainweb_540p (same
+volume, 960x540), head64 (64^3 float32, 128x128). Prints the mean frame time
+from CUDA events (a number taken under a profiler is not a benchmark value).
+"""
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    import torch
+
+    import paper_2605_19737_gb300 as pkg
+    from phantoms import workloads
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="brainweb_1080p", choices=["brainweb_1080p", "brainweb_540p", "head64"])
+    ap.add_argument("--kernel", default="staged", choices=["gather", "staged"])
+    ap.add_argument("--frames", type=int, default=3)
+    ap.add_argument("--packet-w", type=int, default=8)
+    ap.add_argument("--warps", type=int, default=4)
+    args = ap.parse_args()
+    if args.workload == "head64":
+        case = workloads.head64_128px()
+    elif args.workload == "brainweb_540p":
+        case = workloads.brainweb_1080p(width=960, height=540)
+    else:
+        case = workloads.brainweb_1080p()
+    kernel = pkg.VR_KERNEL_STAGED if args.kernel == "staged" else pkg.VR_KERNEL_GATHER
+    vol = case["volume"]
+    data = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
+    with pkg.Context(0) as ctx:
+        vid = ctx.load_volume(data, case["spacing"])
+        ctx.precompute_morphology(vid, case["sigmas"])
+        ctx.set_tissue_params(vid, case["tf"], **case["params"])
+        out = torch.empty((case["cams"].shape[0], case["H"], case["W"], 4), device="cuda")
+        ts = []
+        for _ in range(args.frames):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            ctx.render(vid, case["cams"], case["W"], case["H"], out=out, kernel=kernel, packet_w=args.packet_w,
+                       warps_per_block=args.warps)
+            e.record()
+            ctx.synchronize()
+            ts.append(s.elapsed_time(e))
+    print("%s %s: %.3f ms/frame (mean of %d)" % (args.workload, args.kernel, float(np.mean(ts)), len(ts)))
+
+
+if __name__ == "__main__":
+    main()

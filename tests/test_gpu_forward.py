@@ -90,11 +90,15 @@ def test_classification_bit_exact(vr, torch):
     vr.free_volume(vid)
 
 
-def test_head64_parity_and_counts(vr, torch):
+KERNELS = [1, 2]  # VR_KERNEL_GATHER, VR_KERNEL_STAGED
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_head64_parity_and_counts(vr, torch, kernel):
     """The head phantom workload (64^3 float32, 128x128, 1D TF, Phong, ET 0.99)."""
     case = workloads.head64_128px()
     vid = _load_case(vr, torch, case)
-    img, rs = _render(vr, torch, vid, case)
+    img, rs = _render(vr, torch, vid, case, kernel=kernel)
     _, empty = vr.get_bricks(vid)
     res = oracle_render_case(case, brick_empty=empty)
     err, nflag = assert_rgba_parity(img, res, what="head64")
@@ -104,15 +108,16 @@ def test_head64_parity_and_counts(vr, torch):
     vr.free_volume(vid)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("kappa", [False, True])
-def test_brainweb_small_mode1_parity(vr, torch, kappa):
+def test_brainweb_small_mode1_parity(vr, torch, kappa, kernel):
     """uint16 BrainWeb-shaped volume, 2D gradient TF, curvature-modulated opacity,
     3 cameras, ragged 100x75 image (several tiles plus partial ones)."""
     case = workloads.scaled_brainweb((61, 73, 59), width=100, height=75, n_cams=3)
     if not kappa:
         case["params"] = dict(case["params"], gamma=0.0)
     vid = _load_case(vr, torch, case)
-    img, rs = _render(vr, torch, vid, case)
+    img, rs = _render(vr, torch, vid, case, kernel=kernel)
     _, empty = vr.get_bricks(vid)
     res = oracle_render_case(case, brick_empty=empty)
     assert_rgba_parity(img, res, what="brainweb small")
@@ -120,7 +125,8 @@ def test_brainweb_small_mode1_parity(vr, torch, kappa):
     vr.free_volume(vid)
 
 
-def test_anisotropic_spacing_grad_mod(vr, torch):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_anisotropic_spacing_grad_mod(vr, torch, kernel):
     rng = np.random.default_rng(41)
     dims, sp = (30, 26, 22), (0.8, 1.1, 1.4)
     vol = ph.head_phantom(dims, seed=41)
@@ -131,7 +137,7 @@ def test_anisotropic_spacing_grad_mod(vr, torch):
                                et_threshold=0.95, step_vox=0.37)
     case = dict(volume=vol, spacing=sp, cams=cams, W=40, H=33, tf=tf, params=params)
     vid = _load_case(vr, torch, case)
-    img, rs = _render(vr, torch, vid, case)
+    img, rs = _render(vr, torch, vid, case, kernel=kernel)
     _, empty = vr.get_bricks(vid)
     res = oracle_render_case(case, brick_empty=empty)
     assert_rgba_parity(img, res, what="anisotropic")
@@ -139,16 +145,30 @@ def test_anisotropic_spacing_grad_mod(vr, torch):
     vr.free_volume(vid)
 
 
-def test_skip_is_bit_neutral_and_deterministic(vr, torch):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_skip_is_bit_neutral_and_deterministic(vr, torch, kernel):
     case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
     vid = _load_case(vr, torch, case)
-    a, ra = _render(vr, torch, vid, case, skip_empty=True)
-    b, rb = _render(vr, torch, vid, case, skip_empty=False)
-    c, _ = _render(vr, torch, vid, case, skip_empty=True)
+    a, ra = _render(vr, torch, vid, case, skip_empty=True, kernel=kernel)
+    b, rb = _render(vr, torch, vid, case, skip_empty=False, kernel=kernel)
+    c, _ = _render(vr, torch, vid, case, skip_empty=True, kernel=kernel)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
     np.testing.assert_array_equal(ra[..., 0], rb[..., 0])
     assert ra[..., 1].sum() < rb[..., 1].sum()  # skipping evaluated fewer samples
+    vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("packet_w,warps", [(8, 4), (4, 8), (16, 2), (32, 1), (8, 8)])
+def test_staged_equals_gather_bitwise(vr, torch, packet_w, warps):
+    """Brick staging changes only where voxels are read from, never the arithmetic:
+    images and per-ray sample counts are bit-identical for every packet shape."""
+    case = workloads.scaled_brainweb((61, 73, 59), width=100, height=75, n_cams=3)
+    vid = _load_case(vr, torch, case)
+    a, ra = _render(vr, torch, vid, case, kernel=1)
+    b, rb = _render(vr, torch, vid, case, kernel=2, packet_w=packet_w, warps_per_block=warps)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ra, rb)
     vr.free_volume(vid)
 
 
@@ -172,11 +192,12 @@ def test_counters_match_ray_samples(vr, torch):
     vid = _load_case(vr, torch, case)
     ctr = pkg.new_counters()
     rs = torch.zeros((1, 128, 128, 2), dtype=torch.int32, device="cuda")
-    vr.render(vid, case["cams"], 128, 128, counters=ctr, ray_samples=rs)
+    vr.render(vid, case["cams"], 128, 128, counters=ctr, ray_samples=rs, kernel=2)
     c = ctr.cpu().numpy()
     r = rs.cpu().numpy().astype(np.int64)
     assert c[1] == r[..., 0].sum() and c[2] == r[..., 1].sum()
     assert c[0] == int((r[..., 0] > 0).sum())
+    assert c[3] > 0  # bricks staged into shared memory
     vr.free_volume(vid)
 
 
