@@ -30,6 +30,7 @@ struct Volume {
     float* d_minmax = nullptr;
     float* d_vessel = nullptr;
     float* d_vbricks = nullptr;
+    float* d_smax = nullptr;  // per-scale max Hessian norm (8 floats)
     float* d_tf = nullptr;
     size_t tf_cap = 0;
     int* d_prefix = nullptr;
@@ -50,6 +51,8 @@ struct vr_ctx {
     int partials_cap = 0;
     void* d_stage = nullptr;
     size_t stage_cap = 0;
+    float* d_scratch = nullptr;   // vesselness smoothing scratch (2 volumes)
+    size_t scratch_cap = 0;
     unsigned* d_work = nullptr;   // [0]: staged-kernel work counter, [1]: status word
     int staged_ctas[2][17] = {};   // resident CTAs per SM by (vesselness, warps per block)
 };
@@ -95,6 +98,7 @@ void free_volume(Volume* v) {
     cudaFree(v->d_minmax);
     cudaFree(v->d_vessel);
     cudaFree(v->d_vbricks);
+    cudaFree(v->d_smax);
     cudaFree(v->d_tf);
     cudaFree(v->d_prefix);
     delete v;
@@ -173,6 +177,7 @@ vr_status vr_destroy(vr_ctx* ctx) {
     for (auto& kv : ctx->vols) free_volume(kv.second);
     cudaFree(ctx->d_partials);
     cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_scratch);
     cudaFree(ctx->d_work);
     (void)cudaGetLastError();
     delete ctx;
@@ -305,9 +310,28 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     for (int i = 0; i < n_sigmas; ++i)
         if (!(h_sigmas[i] > 0.0f && h_sigmas[i] <= 8.0f))
             return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: sigma %g outside (0, 8]", (double)h_sigmas[i]);
-    if (n_sigmas > 0) return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: vesselness not built yet");
     DeviceGuard g(ctx->device);
     CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
+    if (n_sigmas > 0) {
+        if (!v->d_vessel) {
+            CK(dalloc(&v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
+            CK(dalloc(&v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
+            CK(dalloc(&v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
+        }
+        const size_t need = sizeof(float) * 2 * (size_t)v->nvox;
+        if (ctx->scratch_cap < need) {
+            CK(cudaStreamSynchronize(ctx->stream), "vesselness scratch sync");
+            cudaFree(ctx->d_scratch);
+            ctx->d_scratch = nullptr;
+            ctx->scratch_cap = 0;
+            CK(dalloc(&ctx->d_scratch, need), "vesselness scratch");
+            ctx->scratch_cap = need;
+        }
+        CK(launch_frangi(v->d_norm, v->n, h_sigmas, n_sigmas, ctx->d_scratch, ctx->d_scratch + v->nvox, v->d_smax,
+                         v->d_vessel, ctx->stream),
+           "vesselness");
+        CK(launch_make_bricks(v->d_vessel, v->n, v->nb, v->d_vbricks, ctx->stream), "vesselness bricks");
+    }
     v->morph_ready = true;
     return VR_OK;
 }

@@ -79,6 +79,11 @@ cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], Vol
 cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
                             uint8_t* empty, int* prefix_scratch /* tf_w + 1 ints */, cudaStream_t st);
 
+// Multi-scale vesselness of `norm` into V (both nvox floats); tmp_a/tmp_b are
+// nvox-float scratch volumes, smax receives each scale's max Hessian norm.
+cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas, int n_sigmas, float* tmp_a,
+                          float* tmp_b, float* smax, float* V, cudaStream_t st);
+
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
 int staged_smem_bytes(int warps_per_block, bool vessel);

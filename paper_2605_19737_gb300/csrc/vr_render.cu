@@ -305,7 +305,9 @@ cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int
 
 cudaError_t staged_config(int warps_per_block, bool vessel, int* ctas_per_sm) {
     const int smem = staged_smem_bytes(warps_per_block, vessel);
-    cudaError_t e = cudaFuncSetAttribute(k_render_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // One limit for every configuration (the largest), so a later call can never lower it.
+    cudaError_t e = cudaFuncSetAttribute(k_render_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         staged_smem_bytes(8, true));
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_render_staged, warps_per_block * 32, smem);
 }
