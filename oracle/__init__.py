@@ -75,6 +75,8 @@ def _load():
         L.or_frangi_response.argtypes = [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.or_frangi_response.restype = ctypes.c_double
         L.or_frangi.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]
+        L.or_render_grad.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
         L.or_sample_points.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P,
                                        ctypes.c_int64, _P, _P]
     return _lib
@@ -236,6 +238,25 @@ def sample_points(In, spacing, params, tf, points, direction, V=None, gmax_value
                        _ptr(_c(tf, np.float32)), float(gmax_value), _ptr(pts), pts.shape[0],
                        _ptr(_c(direction, np.float64)), _ptr(out))
     return out
+
+
+def render_grad(In, spacing, params, tf, cams, W, H, dl_drgba, V=None, gmax_value=0.0, want_volume=True):
+    """FP64 gradient of sum(dl_drgba * RGBA) -> (dtf like tf, dparams[gamma, ka, kd, ks, opacity_scale],
+    dIn like In or None)."""
+    L = _load()
+    In = _c(In, np.float64)
+    Vc = None if V is None else _c(V, np.float64)
+    tf32 = _c(tf, np.float32)
+    cams = _c(cams, np.float32).reshape(-1, 12)
+    dl = _c(dl_drgba, np.float64)
+    assert dl.shape == (cams.shape[0], H, W, 4)
+    dtf = np.zeros(tf32.shape, np.float64)
+    dpar = np.zeros(5)
+    dIn = np.zeros_like(In) if want_volume else None
+    L.or_render_grad(_ptr(In), _ptr(Vc), _ptr(_dims(In)), _ptr(_c(spacing, np.float64)), ctypes.byref(params),
+                     _ptr(tf32), float(gmax_value), _ptr(cams), cams.shape[0], W, H, _ptr(dl), _ptr(dtf), _ptr(dpar),
+                     _ptr(dIn))
+    return dtf, dpar, dIn
 
 
 # ------------------------------------------------------- bricks and skipping

@@ -776,3 +776,282 @@ void or_sample_points(const double *In, const double *V, const int *n, const dou
     free(g);
     free(Hs);
 }
+
+/* ------------------------------------------------------------ gradients */
+
+/* Everything the adjoint of one sample needs, evaluated in FP64 at world point p. */
+typedef struct {
+    int i0[3];
+    double f[3];
+    double fld[11];   /* I, g3, H6 (xx yy zz xy xz yz), V */
+    double gmag, gg, kappa, ghat[3], gn, y, rgba[4];
+    int tj, tk;       /* transfer-function cell */
+    double tt, tq;    /* its fractions */
+    int clamp_x, clamp_y; /* 1 when the lookup coordinate lies inside [0, 1] */
+    double mg, w_inner, w, raw, alpha, d, dot, c[3];
+} or_srec;
+
+static void sample_record(const or_vol *v, const or_params *P, const double *tf, const double p[3],
+                          const double dir[3], or_srec *s) {
+    memset(s, 0, sizeof *s);
+    for (int a = 0; a < 3; ++a) cell_of(p[a] / v->s[a] - 0.5, v->n[a], &s->i0[a], &s->f[a]);
+    field_at(v, p, s->fld);
+    const double *g = s->fld + 1, *H = s->fld + 4;
+    s->gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    s->gmag = sqrt(s->gg);
+    if (s->gg > 0.0) {
+        double km[2];
+        or_curvature(g, H, km);
+        s->kappa = km[0];
+        for (int a = 0; a < 3; ++a) s->ghat[a] = g[a] / s->gmag;
+    }
+    s->gn = v->gmax > 0.0 ? s->gmag / v->gmax : 0.0;
+    s->y = P->tf_mode == 1 ? s->gn : (P->tf_mode == 2 ? s->fld[10] : 0.0);
+    double I = s->fld[0];
+    s->clamp_x = I >= 0.0 && I <= 1.0;
+    double xs = clampd(I, 0.0, 1.0) * (P->tf_w - 1);
+    s->tj = (int)floor(xs);
+    if (s->tj > P->tf_w - 2) s->tj = P->tf_w - 2;
+    s->tt = xs - s->tj;
+    if (P->tf_h > 1) {
+        s->clamp_y = s->y >= 0.0 && s->y <= 1.0;
+        double ys = clampd(s->y, 0.0, 1.0) * (P->tf_h - 1);
+        s->tk = (int)floor(ys);
+        if (s->tk > P->tf_h - 2) s->tk = P->tf_h - 2;
+        s->tq = ys - s->tk;
+    }
+    tf_sample(tf, P->tf_w, P->tf_h, I, s->y, s->rgba);
+    s->mg = P->grad_mod ? (s->gn < 1.0 ? s->gn : 1.0) : 1.0;
+    s->w_inner = 1.0 + P->gamma * s->kappa / P->kappa_ref;
+    s->w = clampd(s->w_inner, 0.0, P->w_max);
+    s->raw = P->opacity_scale * s->rgba[3] * s->mg * s->w;
+    s->alpha = clampd(s->raw, 0.0, 1.0);
+    s->dot = s->ghat[0] * dir[0] + s->ghat[1] * dir[1] + s->ghat[2] * dir[2];
+    s->d = fabs(s->dot);
+    double d16 = pow(s->d, 16.0);
+    for (int q = 0; q < 3; ++q)
+        s->c[q] = P->shading ? s->rgba[q] * (P->ka + P->kd * s->d) + P->ks * d16 : s->rgba[q];
+}
+
+/* Chain dL/dalpha and dL/dc of one sample back to the transfer-function entries,
+ * the uniforms (gamma, ka, kd, ks, opacity_scale) and the per-voxel adjoints of the
+ * interpolated fields (I_norm, gradient, Hessian), following Eq. 4, the lookup,
+ * the shading, Eq. 3 and the trilinear weights; clamps pass gradient only on
+ * their identity branch, |x| has derivative sign(x) (0 at 0). */
+static void sample_adjoint(const or_vol *v, const or_params *P, const double *tf, const or_srec *s,
+                           const double dir[3], double da, const double dc[3], double *dtf, double *dpar,
+                           double *aI, double *ag, double *aH) {
+    (void)tf;
+    const double *g = s->fld + 1, *H = s->fld + 4;
+    double drgba[4] = {0, 0, 0, 0}, dd = 0.0;
+    /* colour */
+    double d15 = pow(s->d, 15.0), d16 = d15 * s->d;
+    for (int q = 0; q < 3; ++q) {
+        if (P->shading) {
+            drgba[q] += dc[q] * (P->ka + P->kd * s->d);
+            dpar[1] += dc[q] * s->rgba[q];
+            dpar[2] += dc[q] * s->rgba[q] * s->d;
+            dpar[3] += dc[q] * d16;
+            dd += dc[q] * (s->rgba[q] * P->kd + 16.0 * P->ks * d15);
+        } else {
+            drgba[q] += dc[q];
+        }
+    }
+    /* opacity, Eq. 4 */
+    double draw = (s->raw >= 0.0 && s->raw <= 1.0) ? da : 0.0;
+    dpar[4] += draw * s->rgba[3] * s->mg * s->w;
+    drgba[3] += draw * P->opacity_scale * s->mg * s->w;
+    double dmg = draw * P->opacity_scale * s->rgba[3] * s->w;
+    double dw = draw * P->opacity_scale * s->rgba[3] * s->mg;
+    double dwi = (s->w_inner >= 0.0 && s->w_inner <= P->w_max) ? dw : 0.0;
+    dpar[0] += dwi * s->kappa / P->kappa_ref;
+    double dkappa = dwi * P->gamma / P->kappa_ref;
+    double dgn = 0.0;
+    if (P->grad_mod && s->gn < 1.0) dgn += dmg;
+    /* transfer-function lookup */
+    double dI = 0.0, dy = 0.0;
+    int w = P->tf_w;
+    if (P->tf_h == 1) {
+        for (int c = 0; c < 4; ++c) {
+            dtf[4 * s->tj + c] += (1.0 - s->tt) * drgba[c];
+            dtf[4 * (s->tj + 1) + c] += s->tt * drgba[c];
+            if (s->clamp_x) dI += drgba[c] * (tf[4 * (s->tj + 1) + c] - tf[4 * s->tj + c]) * (w - 1);
+        }
+    } else {
+        int j = s->tj, k = s->tk;
+        double t = s->tt, q = s->tq;
+        for (int c = 0; c < 4; ++c) {
+            double T00 = tf[4 * (k * w + j) + c], T01 = tf[4 * (k * w + j + 1) + c];
+            double T10 = tf[4 * ((k + 1) * w + j) + c], T11 = tf[4 * ((k + 1) * w + j + 1) + c];
+            dtf[4 * (k * w + j) + c] += (1.0 - q) * (1.0 - t) * drgba[c];
+            dtf[4 * (k * w + j + 1) + c] += (1.0 - q) * t * drgba[c];
+            dtf[4 * ((k + 1) * w + j) + c] += q * (1.0 - t) * drgba[c];
+            dtf[4 * ((k + 1) * w + j + 1) + c] += q * t * drgba[c];
+            if (s->clamp_x) dI += drgba[c] * ((1.0 - q) * (T01 - T00) + q * (T11 - T10)) * (w - 1);
+            if (s->clamp_y) dy += drgba[c] * ((1.0 - t) * (T10 - T00) + t * (T11 - T01)) * (P->tf_h - 1);
+        }
+        if (P->tf_mode == 1) dgn += dy; /* mode 2: V is a constant of the volume */
+    }
+    /* shading direction d = |g-hat . dir| and curvature kappa = g^T H g / |g|^2 */
+    double dgv[3] = {0, 0, 0}, dHv[6] = {0, 0, 0, 0, 0, 0};
+    if (s->gg > 0.0) {
+        double sgn = s->dot > 0.0 ? 1.0 : (s->dot < 0.0 ? -1.0 : 0.0);
+        double dghat[3];
+        for (int a = 0; a < 3; ++a) dghat[a] = P->shading ? dd * sgn * dir[a] : 0.0;
+        double proj = dghat[0] * s->ghat[0] + dghat[1] * s->ghat[1] + dghat[2] * s->ghat[2];
+        for (int a = 0; a < 3; ++a) dgv[a] += (dghat[a] - proj * s->ghat[a]) / s->gmag;
+        for (int a = 0; a < 3; ++a) dgv[a] += dgn * s->ghat[a] / (v->gmax > 0.0 ? v->gmax : 1.0) * (v->gmax > 0.0);
+        double Hg[3] = {H[0] * g[0] + H[3] * g[1] + H[4] * g[2], H[3] * g[0] + H[1] * g[1] + H[5] * g[2],
+                        H[4] * g[0] + H[5] * g[1] + H[2] * g[2]};
+        for (int a = 0; a < 3; ++a) dgv[a] += dkappa * (2.0 * Hg[a] - 2.0 * s->kappa * g[a]) / s->gg;
+        dHv[0] += dkappa * g[0] * g[0] / s->gg;
+        dHv[1] += dkappa * g[1] * g[1] / s->gg;
+        dHv[2] += dkappa * g[2] * g[2] / s->gg;
+        dHv[3] += dkappa * 2.0 * g[0] * g[1] / s->gg;
+        dHv[4] += dkappa * 2.0 * g[0] * g[2] / s->gg;
+        dHv[5] += dkappa * 2.0 * g[1] * g[2] / s->gg;
+    }
+    /* trilinear weights onto the voxel fields */
+    for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy2 = (c >> 1) & 1, dz = (c >> 2) & 1;
+        double wt = (dx ? s->f[0] : 1.0 - s->f[0]) * (dy2 ? s->f[1] : 1.0 - s->f[1]) * (dz ? s->f[2] : 1.0 - s->f[2]);
+        int64_t id = vidx(v->n, s->i0[0] + dx, s->i0[1] + dy2, s->i0[2] + dz);
+        aI[id] += wt * dI;
+        for (int q = 0; q < 3; ++q) ag[3 * id + q] += wt * dgv[q];
+        for (int q = 0; q < 6; ++q) aH[6 * id + q] += wt * dHv[q];
+    }
+}
+
+/* Transpose of the voxel stencils of Eq. 2 and Sec. 2.3 (clamp-to-edge): add the
+ * adjoints of the voxel gradient and Hessian into the adjoint of I_norm. */
+static void stencil_adjoint(const int *n, const double *s, const double *ag, const double *aH, double *dIn) {
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                int im = clampi(i - 1, 0, n[0] - 1), ip = clampi(i + 1, 0, n[0] - 1);
+                int jm = clampi(j - 1, 0, n[1] - 1), jp = clampi(j + 1, 0, n[1] - 1);
+                int km = clampi(k - 1, 0, n[2] - 1), kp = clampi(k + 1, 0, n[2] - 1);
+                int64_t v = vidx(n, i, j, k);
+                const double *G = ag + 3 * v, *Hh = aH + 6 * v;
+                dIn[vidx(n, ip, j, k)] += G[0] / (2.0 * s[0]);
+                dIn[vidx(n, im, j, k)] -= G[0] / (2.0 * s[0]);
+                dIn[vidx(n, i, jp, k)] += G[1] / (2.0 * s[1]);
+                dIn[vidx(n, i, jm, k)] -= G[1] / (2.0 * s[1]);
+                dIn[vidx(n, i, j, kp)] += G[2] / (2.0 * s[2]);
+                dIn[vidx(n, i, j, km)] -= G[2] / (2.0 * s[2]);
+                double hx = Hh[0] / (s[0] * s[0]), hy = Hh[1] / (s[1] * s[1]), hz = Hh[2] / (s[2] * s[2]);
+                dIn[vidx(n, ip, j, k)] += hx;
+                dIn[v] -= 2.0 * hx;
+                dIn[vidx(n, im, j, k)] += hx;
+                dIn[vidx(n, i, jp, k)] += hy;
+                dIn[v] -= 2.0 * hy;
+                dIn[vidx(n, i, jm, k)] += hy;
+                dIn[vidx(n, i, j, kp)] += hz;
+                dIn[v] -= 2.0 * hz;
+                dIn[vidx(n, i, j, km)] += hz;
+                double hxy = Hh[3] / (4.0 * s[0] * s[1]), hxz = Hh[4] / (4.0 * s[0] * s[2]);
+                double hyz = Hh[5] / (4.0 * s[1] * s[2]);
+                dIn[vidx(n, ip, jp, k)] += hxy;
+                dIn[vidx(n, ip, jm, k)] -= hxy;
+                dIn[vidx(n, im, jp, k)] -= hxy;
+                dIn[vidx(n, im, jm, k)] += hxy;
+                dIn[vidx(n, ip, j, kp)] += hxz;
+                dIn[vidx(n, ip, j, km)] -= hxz;
+                dIn[vidx(n, im, j, kp)] -= hxz;
+                dIn[vidx(n, im, j, km)] += hxz;
+                dIn[vidx(n, i, jp, kp)] += hyz;
+                dIn[vidx(n, i, jp, km)] -= hyz;
+                dIn[vidx(n, i, jm, kp)] -= hyz;
+                dIn[vidx(n, i, jm, km)] += hyz;
+            }
+}
+
+/* Gradient of L = sum_pixels <dL/dRGBA, RGBA> (any loss through its image
+ * gradient dl_drgba) with respect to the transfer-function entries (dtf, same
+ * layout as tf), the uniforms dpar = (gamma, ka, kd, ks, opacity_scale) and the
+ * normalised voxel intensities (dIn, may be NULL). The stopping sample of every
+ * ray is the forward one (a fixed index); I_min, I_max, |grad I|_max (gmax) and V
+ * are constants. Compositing adjoint (Eqs. 5-6): with T_k = prod_{j<k}(1 - a_j),
+ * dC/da_k = T_k (c_k - R_{k+1}), R_{k+1} the colour composited from k+1 onwards,
+ * dA/da_k = T_k prod_{j>k}(1 - a_j), dC/dc_k = T_k a_k. Serial (plain and slow). */
+void or_render_grad(const double *In, const double *V, const int *n, const double *s, const or_params *P,
+                    const float *tf32, double gmax, const float *cams, int n_cams, int W, int H,
+                    const double *dl_drgba, double *dtf, double *dpar, double *dIn) {
+    or_vol v;
+    make_vol(&v, In, V, n, s);
+    int64_t nvox = (int64_t)n[0] * n[1] * n[2];
+    double *g = (double *)malloc(sizeof(double) * 3 * nvox), *Hs = (double *)malloc(sizeof(double) * 6 * nvox);
+    or_voxel_derivatives(In, n, s, g, Hs);
+    v.g = g;
+    v.H = Hs;
+    v.gmax = gmax > 0.0 ? gmax : or_gmax(g, nvox);
+    int ntf = P->tf_w * P->tf_h * 4;
+    double *tf = (double *)malloc(sizeof(double) * ntf);
+    for (int q = 0; q < ntf; ++q) tf[q] = (double)tf32[q];
+    for (int q = 0; q < ntf; ++q) dtf[q] = 0.0;
+    for (int q = 0; q < 5; ++q) dpar[q] = 0.0;
+    double *aI = (double *)calloc(nvox, sizeof(double));
+    double *ag = (double *)calloc(3 * nvox, sizeof(double));
+    double *aH = (double *)calloc(6 * nvox, sizeof(double));
+    double dt = P->step_vox * fmin(s[0], fmin(s[1], s[2]));
+    int64_t cap = 64;
+    double *al = (double *)malloc(sizeof(double) * cap), *cl = (double *)malloc(sizeof(double) * 3 * cap);
+    for (int ci = 0; ci < n_cams; ++ci) {
+        double cam[12];
+        for (int q = 0; q < 12; ++q) cam[q] = (double)cams[12 * ci + q];
+        for (int j = 0; j < H; ++j)
+            for (int i = 0; i < W; ++i) {
+                int64_t pix = ((int64_t)ci * H + j) * W + i;
+                const double *dl = dl_drgba + 4 * pix;
+                double o[3], d[3], tn, tfar;
+                if (!ray_setup(&v, cam, W, H, i, j, o, d, &tn, &tfar)) continue;
+                /* forward: the processed samples and their (alpha, colour) */
+                int64_t ns = 0;
+                double A = 0.0;
+                for (int64_t k = 0; tn + (k + 0.5) * dt < tfar; ++k) {
+                    double t = tn + (k + 0.5) * dt, p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                    or_srec sr;
+                    sample_record(&v, P, tf, p, d, &sr);
+                    if (ns == cap) {
+                        cap *= 2;
+                        al = (double *)realloc(al, sizeof(double) * cap);
+                        cl = (double *)realloc(cl, sizeof(double) * 3 * cap);
+                    }
+                    al[ns] = sr.alpha;
+                    for (int q = 0; q < 3; ++q) cl[3 * ns + q] = sr.c[q];
+                    ++ns;
+                    A = A + (1.0 - A) * sr.alpha;
+                    if (A >= P->et_threshold) break;
+                }
+                /* reverse: R_{k+1}, prod_{j>k}(1 - a_j), T_k from the forward prefix products */
+                double *T = (double *)malloc(sizeof(double) * (ns + 1));
+                T[0] = 1.0;
+                for (int64_t k = 0; k < ns; ++k) T[k + 1] = T[k] * (1.0 - al[k]);
+                double R[3] = {0, 0, 0}, Pk = 1.0;
+                for (int64_t k = ns - 1; k >= 0; --k) {
+                    double da = T[k] * (dl[0] * (cl[3 * k] - R[0]) + dl[1] * (cl[3 * k + 1] - R[1]) +
+                                        dl[2] * (cl[3 * k + 2] - R[2]) + dl[3] * Pk);
+                    double dc[3] = {T[k] * al[k] * dl[0], T[k] * al[k] * dl[1], T[k] * al[k] * dl[2]};
+                    double t = tn + (k + 0.5) * dt, p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+                    or_srec sr;
+                    sample_record(&v, P, tf, p, d, &sr);
+                    sample_adjoint(&v, P, tf, &sr, d, da, dc, dtf, dpar, aI, ag, aH);
+                    for (int q = 0; q < 3; ++q) R[q] = al[k] * cl[3 * k + q] + (1.0 - al[k]) * R[q];
+                    Pk *= (1.0 - al[k]);
+                }
+                free(T);
+            }
+    }
+    if (dIn) {
+        for (int64_t q = 0; q < nvox; ++q) dIn[q] = aI[q];
+        stencil_adjoint(n, s, ag, aH, dIn);
+    }
+    free(al);
+    free(cl);
+    free(aI);
+    free(ag);
+    free(aH);
+    free(tf);
+    free(g);
+    free(Hs);
+}

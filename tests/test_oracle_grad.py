@@ -1,0 +1,83 @@
+"""Pins of the oracle's FP64 gradient against central finite differences of its own
+forward renderer (a different code path: the forward never differentiates).
+
+L = sum(dl * RGBA) with a seeded random dl; directional derivatives along
+seeded random directions over all transfer-function entries, over all voxels,
+and per uniform. The steps are small enough that no sample crosses a clamp,
+a transfer-function segment boundary or an early-termination decision.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import phantoms as ph
+
+
+def _case(mode, seed=61, shading=1, et=2.0):
+    rng = np.random.default_rng(seed)
+    dims, sp = (10, 9, 8), (1.0, 0.9, 1.1)
+    In = ph.random_volume(dims, seed, np.float64, smooth=2)
+    In = (In - In.min()) / (In.max() - In.min())
+    cams = ph.camera_array([ph.orbit_camera(dims, sp, az, el, width=12, height=10) for az, el in ((25, 15), (210, -30))])
+    h = 1 if mode == 0 else 6
+    tf = rng.random((h, 16, 4)).astype(np.float32)
+    tf[..., 3] *= 0.25
+    pars = dict(tf_mode=mode, tf_w=16, tf_h=h, grad_mod=1 if mode == 0 else 0, shading=shading, gamma=0.3,
+                kappa_ref=2.0, w_max=3.0, ka=0.3, kd=0.6, ks=0.25, opacity_scale=0.9, et_threshold=et, step_vox=0.5)
+    dl = rng.normal(size=(2, 10, 12, 4))
+    return In, sp, cams, tf, pars, dl
+
+
+def _P(p):
+    return oracle.Params(p["tf_mode"], p["tf_w"], p["tf_h"], p["grad_mod"], p["shading"], p["gamma"], p["kappa_ref"],
+                         p["w_max"], p["ka"], p["kd"], p["ks"], p["opacity_scale"], p["et_threshold"], p["step_vox"])
+
+
+def _loss(In, sp, cams, tf, pars, dl, gmax):
+    r = oracle.render(In, sp, _P(pars), tf, cams, 12, 10, gmax_value=gmax, alternatives=False)
+    return float(np.sum(dl * r.rgba))
+
+
+@pytest.mark.parametrize("mode,shading,et", [(0, 1, 2.0), (1, 1, 2.0), (0, 0, 2.0), (0, 1, 0.9)])
+def test_oracle_gradient_matches_finite_differences(mode, shading, et):
+    In, sp, cams, tf, pars, dl = _case(mode, shading=shading, et=et)
+    gmax = oracle.gmax(In, sp)
+    dtf, dpar, dIn = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, dl, gmax_value=gmax)
+    assert np.abs(dtf).max() > 0 and np.abs(dIn).max() > 0
+    rng = np.random.default_rng(62)
+    # transfer-function entries: step on the float32 table, compare with the exact realised step
+    u = rng.normal(size=tf.shape)
+    hstep = 1e-4
+    tp = (tf.astype(np.float64) + hstep * u).astype(np.float32)
+    tm = (tf.astype(np.float64) - hstep * u).astype(np.float32)
+    fd = (_loss(In, sp, cams, tp, pars, dl, gmax) - _loss(In, sp, cams, tm, pars, dl, gmax))
+    want = float(np.sum(dtf * (tp.astype(np.float64) - tm.astype(np.float64))))
+    assert fd == pytest.approx(want, rel=1e-6, abs=1e-12)
+    # voxels (I_norm, gmax held fixed)
+    u = rng.normal(size=In.shape)
+    h = 1e-7
+    fd = (_loss(In + h * u, sp, cams, tf, pars, dl, gmax) - _loss(In - h * u, sp, cams, tf, pars, dl, gmax)) / (2 * h)
+    assert fd == pytest.approx(float(np.sum(dIn * u)), rel=1e-5, abs=1e-9)
+    # uniforms
+    for idx, name in enumerate(["gamma", "ka", "kd", "ks", "opacity_scale"]):
+        if not shading and name in ("ka", "kd", "ks"):
+            assert dpar[idx] == 0.0
+            continue
+        h = 1e-6
+        pp, pm = dict(pars), dict(pars)
+        pp[name] += h
+        pm[name] -= h
+        fd = (_loss(In, sp, cams, tf, pp, dl, gmax) - _loss(In, sp, cams, tf, pm, dl, gmax)) / (2 * h)
+        assert fd == pytest.approx(dpar[idx], rel=1e-6, abs=1e-9), name
+
+
+def test_gradient_zero_where_transparent():
+    """A zero-opacity transfer function gives zero colour and voxel gradients; the
+    opacity entries still receive gradient (raising them would change the image)."""
+    In, sp, cams, tf, pars, dl = _case(0)
+    tf[..., 3] = 0.0
+    dtf, dpar, dIn = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, dl, gmax_value=oracle.gmax(In, sp))
+    assert np.all(dIn == 0.0)
+    assert np.all(dtf[..., :3] == 0.0) and np.abs(dtf[..., 3]).max() > 0
+    assert dpar[0] == 0.0 and dpar[4] == 0.0
