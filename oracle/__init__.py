@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-FLAG_COUNT, FLAG_ET, FLAG_BRICK = 1, 2, 4
+FLAG_COUNT, FLAG_ET, FLAG_BRICK, FLAG_VAMB = 1, 2, 4, 8
 
 
 def build(force=False):
@@ -62,7 +62,7 @@ def _load():
         L.or_field_brute.argtypes = [_P, _P, _P, _P, _P]
         L.or_curvature.argtypes = [_P, _P, _P]
         L.or_tf_sample.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]
-        L.or_render.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.c_double, _P,
+        L.or_render.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.c_double, _P,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 _P, _P, _P, _P, _P, _P]
         L.or_render.restype = ctypes.c_int
@@ -196,7 +196,7 @@ class RenderResult:
 
 
 def render(In, spacing, params, tf, cams, W, H, V=None, brick_empty=None, gmax_value=0.0, pix_stride=1,
-           alternatives=True):
+           alternatives=True, v_amb=None):
     """Render normalised volume ``In`` for cameras (n, 12) -> RenderResult with (n, H, W, 4) images."""
     L = _load()
     In = _c(In, np.float64)
@@ -211,7 +211,8 @@ def render(In, spacing, params, tf, cams, W, H, V=None, brick_empty=None, gmax_v
     ev = np.zeros((n, H, W), np.int64)
     fl = np.zeros((n, H, W), np.uint8)
     be = None if brick_empty is None else _c(brick_empty, np.uint8)
-    th = L.or_render(_ptr(In), _ptr(Vc), _ptr(_dims(In)), _ptr(_c(spacing, np.float64)), ctypes.byref(params),
+    va = None if v_amb is None else _c(v_amb, np.uint8)
+    th = L.or_render(_ptr(In), _ptr(Vc), _ptr(va), _ptr(_dims(In)), _ptr(_c(spacing, np.float64)), ctypes.byref(params),
                      _ptr(tf32), _ptr(be), float(gmax_value), _ptr(cams), n, W, H, pix_stride,
                      _ptr(rgba), _ptr(lo), _ptr(hi), _ptr(dense), _ptr(ev), _ptr(fl))
     return RenderResult(rgba, lo, hi, dense, ev, fl, th)

@@ -61,11 +61,13 @@ typedef struct {
     double gmax;
     const uint8_t *brick_empty; /* NULL or one byte per brick */
     int nb[3];
+    const uint8_t *v_amb; /* NULL or 1 per voxel where V sits on an eigenvalue tie */
 } or_vol;
 
 #define OR_FLAG_COUNT 1u
 #define OR_FLAG_ET 2u
 #define OR_FLAG_BRICK 4u
+#define OR_FLAG_VAMB 8u /* a sample interpolated V from a tie voxel (vesselness transfer function) */
 
 static inline int64_t vidx(const int *n, int i, int j, int k) {
     return ((int64_t)k * n[1] + j) * n[0] + i;
@@ -377,6 +379,16 @@ static void march(const or_vol *v, const or_params *P, const double *tf, const d
         }
         double alpha, c[3];
         sample_optics(v, P, tf, p, d, &alpha, c);
+        if (flags && v->v_amb && P->tf_mode == 2) {
+            int i0[3];
+            double f[3];
+            for (int a = 0; a < 3; ++a) cell_of(p[a] / v->s[a] - 0.5, v->n[a], &i0[a], &f[a]);
+            for (int cc = 0; cc < 8; ++cc) {
+                int dx = cc & 1, dy = (cc >> 1) & 1, dz = (cc >> 2) & 1;
+                double wt = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                if (wt > 0.0 && v->v_amb[vidx(v->n, i0[0] + dx, i0[1] + dy, i0[2] + dz)]) *flags |= OR_FLAG_VAMB;
+            }
+        }
         for (int q = 0; q < 3; ++q) C[q] = C[q] + (1.0 - A) * c[q] * alpha;  /* Eq. 5 */
         A = A + (1.0 - A) * alpha;                                          /* Eq. 6 */
         if (flags && fabs(A - P->et_threshold) < 1e-5) *flags |= OR_FLAG_ET;
@@ -402,15 +414,18 @@ static void make_vol(or_vol *v, const double *In, const double *V, const int *n,
 }
 
 /* Render n_cams images of W x H premultiplied RGBA (row 0 = top, background 0).
- *   In: normalised volume; V: vesselness or NULL; gmax <= 0: computed here;
+ *   In: normalised volume; V: vesselness or NULL; v_amb: NULL or the tie mask of
+ *   or_frangi (rays that interpolate V from a tie voxel get OR_FLAG_VAMB);
+ *   gmax <= 0: computed here;
  *   brick_empty: NULL or the empty-brick flags (only the evaluated counter uses it);
  *   rgba_lo / rgba_hi (nullable): the outcomes with et -/+ 1e-5 and with one
  *     sample less / more when the count is ambiguous -- every ray whose flags are
  *     non-zero has these alternatives filled, the rest are copies of rgba;
  *   pix_stride > 1 renders only pixels with i % stride == 0 and j % stride == 0.
  * Returns the number of OpenMP threads used. */
-int or_render(const double *In, const double *V, const int *n, const double *s, const or_params *P,
-              const float *tf32, const uint8_t *brick_empty, double gmax_in, const float *cams, int n_cams,
+int or_render(const double *In, const double *V, const uint8_t *v_amb, const int *n, const double *s,
+              const or_params *P, const float *tf32, const uint8_t *brick_empty, double gmax_in, const float *cams,
+              int n_cams,
               int W, int H, int pix_stride, double *rgba, double *rgba_lo, double *rgba_hi, int64_t *dense,
               int64_t *evaluated, uint8_t *flags_out) {
     or_vol v;
@@ -423,6 +438,7 @@ int or_render(const double *In, const double *V, const int *n, const double *s, 
     v.H = Hs;
     v.gmax = gmax_in > 0.0 ? gmax_in : or_gmax(g, nvox);
     v.brick_empty = brick_empty;
+    v.v_amb = v_amb;
     int ntf = P->tf_w * P->tf_h * 4;
     double *tf = (double *)malloc(sizeof(double) * ntf);
     for (int q = 0; q < ntf; ++q) tf[q] = (double)tf32[q];
@@ -696,7 +712,8 @@ double or_frangi_response(const double *l, double alpha, double beta, double c) 
  * Sec. 2.3 in voxel units) times sigma^2, its sorted eigenvalues, c = 0.5 max_v S
  * over the volume, V_sigma by or_frangi_response; V = max over sigma.
  *   smax (nullable): per-scale max S; amb (nullable): 1 where a scale has a
- *   near-tie |l1| ~ |l2| of opposite signs (the response jumps there). */
+ *   near-tie |l1| ~ |l2| (within 1e-4 |l3|) of opposite signs whose other order
+ *   changes that scale's response by more than 5e-5 (the response jumps there). */
 void or_frangi(const double *In, const int *n, const double *sigmas, int ns, double alpha, double beta,
                double *V, double *smax, uint8_t *amb) {
     int64_t nv = (int64_t)n[0] * n[1] * n[2];
@@ -738,8 +755,11 @@ void or_frangi(const double *In, const int *n, const double *sigmas, int ns, dou
             const double *l = lam + 3 * v;
             double r = or_frangi_response(l, alpha, beta, cc);
             if (r > V[v]) V[v] = r;
-            if (amb && (l[0] > 0.0) != (l[1] > 0.0) && fabs(fabs(l[1]) - fabs(l[0])) < 1e-4 * fabs(l[2]))
-                amb[v] = 1;
+            if (amb && (l[0] > 0.0) != (l[1] > 0.0) && fabs(fabs(l[1]) - fabs(l[0])) < 1e-4 * fabs(l[2])) {
+                /* the other order of the tied pair is equally valid; flag only if it matters */
+                double alt[3] = {l[1], l[0], l[2]};
+                if (fabs(or_frangi_response(alt, alpha, beta, cc) - r) > 5e-5) amb[v] = 1;
+            }
         }
     }
     free(sm);
