@@ -277,7 +277,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default="staged", choices=["staged", "gather"])
+    ap.add_argument("--kernel", default="gather", choices=["staged", "gather"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -99,7 +99,7 @@ typedef struct {
 } vr_counters;
 
 typedef enum {
-    VR_KERNEL_AUTO = 0,    /* the fastest available (staged) */
+    VR_KERNEL_AUTO = 0,    /* the fastest measured on GB300 (gather) */
     VR_KERNEL_GATHER = 1,  /* per-lane gathers from the bricked volume in HBM/L2 */
     VR_KERNEL_STAGED = 2   /* warp-cooperative brick staging in shared memory */
 } vr_kernel;
@@ -218,6 +218,24 @@ vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long
 vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
                     int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
                     unsigned int* d_ray_samples);
+
+/* Adjoint of vr_render (the paper renders; differentiating the same
+ * Eqs. 2-6 turns its interactive tissue-parameter tuning into fitting those
+ * parameters to a target view). For a loss L with image gradient
+ * d_dl_drgba = dL/dRGBA ([n_cams][H][W][4] float32, device) of the image
+ * vr_render would produce for the same cameras and uniforms, writes
+ *   d_dtf:     dL/d(transfer-function entries), [tf_h][tf_w][4] float32;
+ *   d_dparams: dL/d(gamma, ka, kd, ks, opacity_scale), 5 float32;
+ *   d_dvolume: NULL or dL/d(normalised voxel intensity), nx*ny*nz float32.
+ * All outputs are device memory and are overwritten. I_min, I_max,
+ * |grad I|_max, the vesselness volume and each ray's stopping sample are
+ * held fixed. Per ray the kernel re-marches forward, then sweeps back to front
+ * rebuilding the transmittance by division (accurate while et_threshold stays
+ * at or below ~0.999), re-evaluating each sample instead of storing it.
+ * opts: NULL or as vr_render (only skip_empty is used). Errors as vr_render. */
+vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
+                             const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
+                             const vr_render_opts* opts);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,7 @@ class Context:
         self._h = h
         self.device = int(device)
         self._keep = {}
+        self._tf_shape = {}
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, st):
@@ -150,6 +151,7 @@ class Context:
         tp = vr_tissue_params(int(tf_mode), w, h, p, int(dev), int(grad_mod), int(shading), gamma, kappa_ref,
                               w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox)
         self._check(self._lib.vr_set_tissue_params(self._h, vol, ctypes.byref(tp)))
+        self._tf_shape[vol] = (h, w)
 
     def get_norm(self, vol):
         a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
@@ -200,6 +202,29 @@ class Context:
                                         counters.data_ptr() if counters is not None else None,
                                         ray_samples.data_ptr() if ray_samples is not None else None))
         return out
+
+
+    def render_backward(self, vol, cams, W, H, dl_drgba, want_volume=True, skip_empty=True, dtf=None, dparams=None,
+                        dvol=None):
+        """Gradients of L given dL/dRGBA (device (n, H, W, 4)): returns (dtf (h, w, 4),
+        dparams (5,) = gamma, ka, kd, ks, opacity_scale, dvolume (nz, ny, nx) or None)."""
+        torch = _torch()
+        carr, n = cameras_to_c(cams)
+        dev = "cuda:%d" % self.device
+        tfh, tfw = self._tf_shape[vol]
+        if dtf is None:
+            dtf = torch.empty((tfh, tfw, 4), dtype=torch.float32, device=dev)
+        if dparams is None:
+            dparams = torch.empty(5, dtype=torch.float32, device=dev)
+        if want_volume and dvol is None:
+            nx, ny, nz = self._keep[vol]
+            dvol = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+        opts = vr_render_opts(VR_KERNEL_GATHER, int(bool(skip_empty)), 8, 4)
+        g = dl_drgba.contiguous()
+        self._check(self._lib.vr_render_backward(self._h, vol, carr, n, W, H, g.data_ptr(), dtf.data_ptr(),
+                                                 dparams.data_ptr(), dvol.data_ptr() if want_volume else None,
+                                                 ctypes.byref(opts)))
+        return dtf, dparams, (dvol if want_volume else None)
 
 
 def new_counters(device=0):

@@ -1,0 +1,237 @@
+// vr_adjoint.cuh -- adjoint of the per-sample math in vr_sample.cuh.
+//
+// Given dL/dalpha and dL/dcolour of one sample, sample_adjoint() walks back
+// through the shading, Eq. 4, the transfer-function lookup and the curvature
+// of Eq. 3 to dL/d(I, grad, Hessian) of the sample field, adding the
+// transfer-function and uniform gradients on the way. field_adjoint_scatter()
+// is the exact transpose of field_eval(): it spreads those field gradients over
+// the 56 weighted voxels of the cell's 4x4x4 neighbourhood. Clamps pass
+// gradient only on their identity branch; |x| has derivative sign(x), 0 at 0.
+#pragma once
+
+#include "vr_sample.cuh"
+
+namespace vr {
+
+struct ParamGrad {
+    float gamma, ka, kd, ks, os;
+};
+
+// Transfer-function gradient sink: shared-memory table (1D) or global atomics.
+struct TfGradSink {
+    float* p;
+    __device__ __forceinline__ void add(int idx, float v) const {
+        if (v != 0.0f) atomicAdd(p + idx, v);
+    }
+};
+
+// dfield receives dL/d(I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz) in the same
+// (spacing-scaled) units as the sample field f.
+__device__ __forceinline__ void sample_adjoint(const float f[10], float vval, const float dir[3], const TissueDev& tp,
+                                               const float4* __restrict__ tf, float inv_gmax, float da,
+                                               const float dc[3], const TfGradSink& dtf, ParamGrad& dp,
+                                               float dfield[10]) {
+    const float gx = f[1], gy = f[2], gz = f[3];
+    const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, Hgx = 0.f, Hgy = 0.f, Hgz = 0.f;
+    if (gg > 0.0f) {
+        gmag = sqrtf(gg);
+        Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
+        Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
+        Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
+        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) / gg;
+        const float inv = 1.0f / gmag;
+        hx = gx * inv;
+        hy = gy * inv;
+        hz = gz * inv;
+    }
+    const float gn = gmag * inv_gmax;
+    const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
+    // transfer-function cell (same arithmetic as tf_lookup)
+    const int w = tp.tf_w, h = tp.tf_h;
+    const float I = f[0];
+    const float xs = fminf(fmaxf(I, 0.0f), 1.0f) * (float)(w - 1);
+    const int j = min((int)xs, w - 2);
+    const float t = xs - (float)j;
+    float4 c, T00, T01, T10 = make_float4(0.f, 0.f, 0.f, 0.f), T11 = T10;
+    int k = 0;
+    float q = 0.0f;
+    T00 = __ldg(tf + j);
+    T01 = __ldg(tf + j + 1);
+    if (h == 1) {
+        c = lerp4(T00, T01, t);
+    } else {
+        const float ys = fminf(fmaxf(y, 0.0f), 1.0f) * (float)(h - 1);
+        k = min((int)ys, h - 2);
+        q = ys - (float)k;
+        const float4* r0 = tf + (long long)k * w + j;
+        T00 = __ldg(r0);
+        T01 = __ldg(r0 + 1);
+        T10 = __ldg(r0 + w);
+        T11 = __ldg(r0 + w + 1);
+        c = lerp4(lerp4(T00, T01, t), lerp4(T10, T11, t), q);
+    }
+    const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
+    const float wi = 1.0f + tp.gamma * kappa / tp.kappa_ref;
+    const float wk = fminf(fmaxf(wi, 0.0f), tp.w_max);
+    const float raw = tp.opacity_scale * c.w * mg * wk;
+    const float dot = fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2]));
+    const float d = fabsf(dot);
+
+    // colour
+    float dr[4] = {0.f, 0.f, 0.f, 0.f}, dd = 0.f;
+    const float crgb[3] = {c.x, c.y, c.z};
+    if (tp.shading) {
+        const float d2 = d * d, d4 = d2 * d2, d8 = d4 * d4, d15 = d8 * d4 * d2 * d, d16 = d8 * d8;
+        const float lit = fmaf(tp.kd, d, tp.ka);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            dr[ch] = dc[ch] * lit;
+            dp.ka += dc[ch] * crgb[ch];
+            dp.kd += dc[ch] * crgb[ch] * d;
+            dp.ks += dc[ch] * d16;
+            dd = fmaf(dc[ch], fmaf(crgb[ch], tp.kd, 16.0f * tp.ks * d15), dd);
+        }
+    } else {
+        dr[0] = dc[0];
+        dr[1] = dc[1];
+        dr[2] = dc[2];
+    }
+    // opacity, Eq. 4
+    const float draw = (raw >= 0.0f && raw <= 1.0f) ? da : 0.0f;
+    dp.os += draw * c.w * mg * wk;
+    dr[3] = draw * tp.opacity_scale * mg * wk;
+    const float dmg = draw * tp.opacity_scale * c.w * wk;
+    const float dw = draw * tp.opacity_scale * c.w * mg;
+    const float dwi = (wi >= 0.0f && wi <= tp.w_max) ? dw : 0.0f;
+    dp.gamma += dwi * kappa / tp.kappa_ref;
+    const float dkappa = dwi * tp.gamma / tp.kappa_ref;
+    float dgn = (tp.grad_mod && gn < 1.0f) ? dmg : 0.0f;
+    // transfer-function lookup
+    const bool in_x = I >= 0.0f && I <= 1.0f;
+    float dI = 0.f;
+    const float T00a[4] = {T00.x, T00.y, T00.z, T00.w}, T01a[4] = {T01.x, T01.y, T01.z, T01.w};
+    if (h == 1) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            dtf.add(4 * j + ch, (1.0f - t) * dr[ch]);
+            dtf.add(4 * (j + 1) + ch, t * dr[ch]);
+            if (in_x) dI = fmaf(dr[ch], (T01a[ch] - T00a[ch]) * (float)(w - 1), dI);
+        }
+    } else {
+        const float T10a[4] = {T10.x, T10.y, T10.z, T10.w}, T11a[4] = {T11.x, T11.y, T11.z, T11.w};
+        const bool in_y = y >= 0.0f && y <= 1.0f;
+        float dy = 0.f;
+        const int e00 = 4 * (k * w + j), e10 = 4 * ((k + 1) * w + j);
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            dtf.add(e00 + ch, (1.0f - q) * (1.0f - t) * dr[ch]);
+            dtf.add(e00 + 4 + ch, (1.0f - q) * t * dr[ch]);
+            dtf.add(e10 + ch, q * (1.0f - t) * dr[ch]);
+            dtf.add(e10 + 4 + ch, q * t * dr[ch]);
+            if (in_x)
+                dI = fmaf(dr[ch], ((1.0f - q) * (T01a[ch] - T00a[ch]) + q * (T11a[ch] - T10a[ch])) * (float)(w - 1),
+                          dI);
+            if (in_y)
+                dy = fmaf(dr[ch], ((1.0f - t) * (T10a[ch] - T00a[ch]) + t * (T11a[ch] - T01a[ch])) * (float)(h - 1),
+                          dy);
+        }
+        if (tp.tf_mode == 1) dgn += dy;  // mode 2: V is a constant of the volume
+    }
+    dfield[0] = dI;
+    float dgx = 0.f, dgy = 0.f, dgz = 0.f;
+#pragma unroll
+    for (int e = 4; e < 10; ++e) dfield[e] = 0.f;
+    if (gg > 0.0f) {
+        if (tp.shading) {
+            const float sgn = dot > 0.0f ? 1.0f : (dot < 0.0f ? -1.0f : 0.0f);
+            const float ax = dd * sgn * dir[0], ay = dd * sgn * dir[1], az = dd * sgn * dir[2];
+            const float proj = fmaf(ax, hx, fmaf(ay, hy, az * hz));
+            const float inv = 1.0f / gmag;
+            dgx += (ax - proj * hx) * inv;
+            dgy += (ay - proj * hy) * inv;
+            dgz += (az - proj * hz) * inv;
+        }
+        dgx = fmaf(dgn * inv_gmax, hx, dgx);
+        dgy = fmaf(dgn * inv_gmax, hy, dgy);
+        dgz = fmaf(dgn * inv_gmax, hz, dgz);
+        const float s = dkappa / gg;
+        dgx = fmaf(2.0f * s, Hgx - kappa * gx, dgx);
+        dgy = fmaf(2.0f * s, Hgy - kappa * gy, dgy);
+        dgz = fmaf(2.0f * s, Hgz - kappa * gz, dgz);
+        dfield[4] = s * gx * gx;
+        dfield[5] = s * gy * gy;
+        dfield[6] = s * gz * gz;
+        dfield[7] = 2.0f * s * gx * gy;
+        dfield[8] = 2.0f * s * gx * gz;
+        dfield[9] = 2.0f * s * gy * gz;
+    }
+    dfield[1] = dgx;
+    dfield[2] = dgy;
+    dfield[3] = dgz;
+}
+
+// Transpose of field_eval + scale_field: add dL/d(voxel) for the 56 weighted voxels.
+// `emit(a, b, c, g)` receives tap (a, b, c) of the 4x4x4 neighbourhood (voxel
+// i0-1+a, j0-1+b, k0-1+c) and its gradient g.
+template <class Emit>
+__device__ __forceinline__ void field_adjoint_scatter(const float dfs[10], const float is[3], float fx, float fy,
+                                                      float fz, const Emit& emit) {
+    // undo the spacing scale (chain through scale_field)
+    const float dI = dfs[0];
+    const float dgx = dfs[1] * is[0], dgy = dfs[2] * is[1], dgz = dfs[3] * is[2];
+    const float dxx = dfs[4] * is[0] * is[0], dyy = dfs[5] * is[1] * is[1], dzz = dfs[6] * is[2] * is[2];
+    const float dxy = dfs[7] * is[0] * is[1], dxz = dfs[8] * is[0] * is[2], dyz = dfs[9] * is[1] * is[2];
+    const float gxw = 1.0f - fx, gyw = 1.0f - fy, gzw = 1.0f - fz;
+    const float w0x[4] = {0.0f, gxw, fx, 0.0f};
+    const float w1x[4] = {-0.5f * gxw, -0.5f * fx, 0.5f * gxw, 0.5f * fx};
+    const float w2x[4] = {gxw, fmaf(3.0f, fx, -2.0f), fmaf(-3.0f, fx, 1.0f), fx};
+    const float w0y[4] = {0.0f, gyw, fy, 0.0f};
+    const float w1y[4] = {-0.5f * gyw, -0.5f * fy, 0.5f * gyw, 0.5f * fy};
+    const float w2y[4] = {gyw, fmaf(3.0f, fy, -2.0f), fmaf(-3.0f, fy, 1.0f), fy};
+    const float w0z[4] = {0.0f, gzw, fz, 0.0f};
+    const float w1z[4] = {-0.5f * gzw, -0.5f * fz, 0.5f * gzw, 0.5f * fz};
+    const float w2z[4] = {gzw, fmaf(3.0f, fz, -2.0f), fmaf(-3.0f, fz, 1.0f), fz};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const bool zmid = (c == 1 || c == 2);
+        // transposed z step: adjoints of the y-level sums A.. of field_eval
+        float A00 = w1z[c] * dgz + w2z[c] * dzz;
+        float A10 = w1z[c] * dxz;
+        float A01 = w1z[c] * dyz;
+        float A20 = 0.f, A11 = 0.f, A02 = 0.f;
+        if (zmid) {
+            A00 = fmaf(w0z[c], dI, A00);
+            A10 = fmaf(w0z[c], dgx, A10);
+            A20 = w0z[c] * dxx;
+            A01 = fmaf(w0z[c], dgy, A01);
+            A11 = w0z[c] * dxy;
+            A02 = w0z[c] * dyy;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const bool ymid = (b == 1 || b == 2);
+            // transposed y step: adjoints of X0, X1, X2
+            float X0 = w1y[b] * A01;
+            float X1 = 0.f, X2 = 0.f;
+            if (ymid) {
+                X0 = fmaf(w0y[b], A00, X0);
+                X1 = w0y[b] * A10;
+                if (zmid) X2 = w0y[b] * A20;
+            }
+            if (zmid) {
+                X1 = fmaf(w1y[b], A11, X1);
+                X0 = fmaf(w2y[b], A02, X0);
+            }
+            // transposed x step
+            if (ymid || zmid) {
+                emit(0, b, c, fmaf(w1x[0], X1, w2x[0] * X2));
+                emit(3, b, c, fmaf(w1x[3], X1, w2x[3] * X2));
+            }
+            emit(1, b, c, fmaf(w0x[1], X0, fmaf(w1x[1], X1, w2x[1] * X2)));
+            emit(2, b, c, fmaf(w0x[2], X0, fmaf(w1x[2], X1, w2x[2] * X2)));
+        }
+    }
+}
+
+}  // namespace vr

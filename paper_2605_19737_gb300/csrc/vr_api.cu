@@ -134,6 +134,23 @@ struct DeviceGuard {
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.0f; }
 
+void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
+    memset(&L, 0, sizeof L);
+    for (int a = 0; a < 3; ++a) {
+        L.vol.n[a] = v->n[a];
+        L.vol.nb[a] = v->nb[a];
+        L.vol.s[a] = v->s[a];
+    }
+    L.vol.bricks = v->d_bricks;
+    L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
+    L.vol.empty = v->d_empty;
+    L.vol.vc = v->d_vc;
+    L.tp = v->tp;
+    L.tf = v->d_tf;
+    L.W = W, L.H = H;
+    L.skip = skip ? 1 : 0;
+}
+
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
     CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
     CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
@@ -486,7 +503,10 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     vr_render_opts o{VR_KERNEL_AUTO, 1, 8, 4};
     if (opts) o = *opts;
     if (o.kernel < 0 || o.kernel > 2) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
-    const bool staged = o.kernel != VR_KERNEL_GATHER;
+    // VR_KERNEL_AUTO picks the per-lane gather kernel: on GB300 the bricked volume stays
+    // L1/L2-resident and per-lane marching keeps 91% of lanes busy, while staging one
+    // brick per warp idles the lanes outside it (ncu: 58% SIMT efficiency).
+    const bool staged = o.kernel == VR_KERNEL_STAGED;
     if (staged && (o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16 && o.packet_w != 32))
         return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8, 16 or 32");
     if (staged && (o.warps_per_block < 1 || o.warps_per_block > 8))
@@ -499,21 +519,10 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         dst = (float*)ctx->d_stage;
     }
     RenderLaunch L;
-    memset(&L, 0, sizeof L);
-    L.vol.n[0] = v->n[0], L.vol.n[1] = v->n[1], L.vol.n[2] = v->n[2];
-    L.vol.nb[0] = v->nb[0], L.vol.nb[1] = v->nb[1], L.vol.nb[2] = v->nb[2];
-    L.vol.s[0] = v->s[0], L.vol.s[1] = v->s[1], L.vol.s[2] = v->s[2];
-    L.vol.bricks = v->d_bricks;
-    L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
-    L.vol.empty = v->d_empty;
-    L.vol.vc = v->d_vc;
-    L.tp = v->tp;
-    L.tf = v->d_tf;
+    fill_launch(L, v, W, H, o.skip_empty);
     L.out = dst;
     L.counters = d_counters;
     L.ray_samples = d_ray_samples;
-    L.W = W, L.H = H;
-    L.skip = o.skip_empty ? 1 : 0;
     L.packet_w = o.packet_w;
     L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
     L.work_counter = ctx->d_work;
@@ -546,6 +555,42 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     }
     if (out_on_host)
         CK(cudaMemcpyAsync(out_rgba, dst, img_bytes, cudaMemcpyDeviceToHost, ctx->stream), "render: copy image back");
+    return VR_OK;
+}
+
+vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
+                             const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
+                             const vr_render_opts* opts) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: unknown id %d", vol_id);
+    if (!h_cams || !d_dl_drgba || !d_dtf || !d_dparams)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: NULL pointer");
+    if (n_cams < 1 || W < 1 || H < 1 || W > 16384 || H > 16384)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: bad image size %d x %d x %d", n_cams, W, H);
+    if (!v->morph_ready) return fail(ctx, VR_ERR_NOT_READY, "render_backward: call vr_precompute_morphology first");
+    if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render_backward: call vr_set_tissue_params first");
+    DeviceGuard g(ctx->device);
+    const int skip = opts ? opts->skip_empty : 1;
+    const size_t ntf = (size_t)v->tp.tf_w * v->tp.tf_h * 4;
+    CK(cudaMemsetAsync(d_dtf, 0, sizeof(float) * ntf, ctx->stream), "render_backward: zero dtf");
+    CK(cudaMemsetAsync(d_dparams, 0, sizeof(float) * 5, ctx->stream), "render_backward: zero dparams");
+    if (d_dvolume) CK(cudaMemsetAsync(d_dvolume, 0, sizeof(float) * v->nvox, ctx->stream), "render_backward: zero dvol");
+    BackwardLaunch B;
+    memset(&B, 0, sizeof B);
+    fill_launch(B.r, v, W, H, skip);
+    B.dl_drgba = d_dl_drgba;
+    B.dtf = d_dtf;
+    B.dparams = d_dparams;
+    B.dvol = d_dvolume;
+    B.tf_in_smem = (v->tp.tf_h == 1 && ntf * sizeof(float) <= 64 * 1024) ? 1 : 0;
+    for (int c0 = 0; c0 < n_cams; c0 += kMaxCamsPerLaunch) {
+        const int nc = n_cams - c0 < kMaxCamsPerLaunch ? n_cams - c0 : kMaxCamsPerLaunch;
+        B.r.n_cams = nc;
+        B.r.cam_offset = c0;
+        memcpy(B.r.cams, h_cams + c0, sizeof(CamDev) * nc);
+        CK(launch_render_backward(B, ctx->stream), "render_backward kernel");
+    }
     return VR_OK;
 }
 

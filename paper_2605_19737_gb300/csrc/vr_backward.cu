@@ -1,0 +1,181 @@
+// vr_backward.cu -- adjoint raymarch: gradients of a loss on the rendered image
+// with respect to the transfer-function entries, the tissue uniforms
+// (gamma, ka, kd, ks, opacity_scale) and the normalised voxel intensities.
+//
+// One thread per ray (the forward kernel's 8x4 warp packets). Per ray:
+//   1. forward re-march with the forward kernel's exact arithmetic, recording the
+//      stopping sample k_stop and the transmittance T before it;
+//   2. reverse sweep k = k_stop .. 0 with no stored samples: the sample is
+//      re-evaluated, T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and
+//      well conditioned because early termination keeps 1 - alpha_k >= 1 - et
+//      before the last sample), R_k = alpha_k c_k + (1 - alpha_k) R_{k+1} and
+//      P_k = prod_{j>k} (1 - alpha_j) are carried backwards, and
+//        dL/dalpha_k = T_k (<dL/dC, c_k - R_{k+1}> + dL/dA P_k),
+//        dL/dc_k     = T_k alpha_k dL/dC              (Eqs. 5-6 differentiated);
+//   3. sample_adjoint / field_adjoint_scatter chain these to the parameters.
+// Transfer-function gradients of a 1D table are summed in shared memory per CTA
+// and flushed with one atomic per non-zero entry; 2D tables and voxels use
+// global atomics; uniform gradients are warp-reduced first.
+#include "vr_adjoint.cuh"
+
+namespace vr {
+
+namespace {
+
+struct GLoad {
+    const float* __restrict__ p;
+    __device__ __forceinline__ float operator()(int o) const { return __ldg(p + o); }
+};
+
+__device__ __forceinline__ long long bidx(const VolumeDev& v, const int b[3]) {
+    return ((long long)b[2] * v.nb[1] + b[1]) * v.nb[0] + b[0];
+}
+
+__global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__ BackwardLaunch B) {
+    extern __shared__ float s_dtf[];
+    const RenderLaunch& L = B.r;
+    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
+    if (B.tf_in_smem) {
+        for (int e = threadIdx.x; e < ntf; e += blockDim.x) s_dtf[e] = 0.0f;
+        __syncthreads();
+    }
+    const TfGradSink sink{B.tf_in_smem ? s_dtf : B.dtf};
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
+    const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
+    const int cam = blockIdx.z;
+    const bool inside = i < L.W && j < L.H;
+    const VolumeDev& v = L.vol;
+    const float4* tf = reinterpret_cast<const float4*>(L.tf);
+    const float gmax = __ldg(&v.vc->gmax);
+    const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+    const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
+    // the reverse sweep divides by 1 - alpha: stop where A reaches 1 even when early termination is off
+    const float et = fminf(L.tp.et_threshold, 1.0f);
+    ParamGrad dp{0.f, 0.f, 0.f, 0.f, 0.f};
+
+    RayDev r;
+    const bool hit = inside && setup_ray(L.cams[cam], L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+    if (hit) {
+        const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
+        const float4 g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
+        // 1. forward re-march
+        float A = 0.f, A_prev = 0.f;
+        int k = 0, kstop = r.ns - 1, klast = -1;
+        while (k < r.ns) {
+            const float kk = (float)k + 0.5f;
+            int i0[3], bc[3];
+            float f[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                bc[q] = i0[q] >> 3;
+            }
+            const long long bi = bidx(v, bc);
+            if (L.skip && __ldg(v.empty + bi)) {
+                k = brick_exit_k(r, bc, k, r.ns);
+                continue;
+            }
+            const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
+                             (i0[0] - kCells * bc[0]);
+            float fld[10];
+            field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+            scale_field(fld, is);
+            const float vval = v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+            float alpha, col[3];
+            sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+            A_prev = A;
+            A += (1.0f - A) * alpha;
+            klast = k;
+            if (A >= et) {
+                kstop = k;
+                break;
+            }
+            ++k;
+        }
+        if (klast >= 0) {
+            // transmittance before the stopping sample
+            float Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
+            float Tk1 = Tk, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;
+            const float dC[3] = {g4.x, g4.y, g4.z};
+            // 2. reverse sweep
+            for (int kr = kstop; kr >= 0; --kr) {
+                const float kk = (float)kr + 0.5f;
+                int i0[3], bc[3];
+                float f[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    bc[q] = i0[q] >> 3;
+                }
+                const long long bi = bidx(v, bc);
+                if (L.skip && __ldg(v.empty + bi)) continue;  // alpha = 0: T, R, P unchanged
+                const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
+                                 (i0[0] - kCells * bc[0]);
+                float fld[10];
+                field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+                scale_field(fld, is);
+                const float vval =
+                    v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+                float alpha, col[3];
+                sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
+                const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
+                                       g4.w * P);
+                const float ta = Tk * alpha;
+                const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
+                float dfs[10];
+                sample_adjoint(fld, vval, r.dir, L.tp, tf, inv_gmax, da, dc, sink, dp, dfs);
+                if (B.dvol) {
+                    const int x0 = i0[0] - 1, y0 = i0[1] - 1, z0 = i0[2] - 1;
+                    const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
+                    float* dv = B.dvol;
+                    field_adjoint_scatter(dfs, is, f[0], f[1], f[2], [&](int a, int b, int c, float g) {
+                        if (g == 0.0f) return;
+                        const int x = min(max(x0 + a, 0), nx - 1), y = min(max(y0 + b, 0), ny - 1),
+                                  z = min(max(z0 + c, 0), nz - 1);
+                        atomicAdd(dv + ((long long)z * ny + y) * nx + x, g);
+                    });
+                }
+                R0 = fmaf(alpha, col[0], (1.0f - alpha) * R0);
+                R1 = fmaf(alpha, col[1], (1.0f - alpha) * R1);
+                R2 = fmaf(alpha, col[2], (1.0f - alpha) * R2);
+                P *= (1.0f - alpha);
+                Tk1 = Tk;
+            }
+        }
+    }
+    // uniform gradients: warp sums, one atomic per warp and parameter
+    float pv[5] = {dp.gamma, dp.ka, dp.kd, dp.ks, dp.os};
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) pv[e] += __shfl_xor_sync(0xffffffffu, pv[e], o);
+    }
+    if (l == 0) {
+#pragma unroll
+        for (int e = 0; e < 5; ++e)
+            if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
+    }
+    if (B.tf_in_smem) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ntf; e += blockDim.x)
+            if (s_dtf[e] != 0.0f) atomicAdd(B.dtf + e, s_dtf[e]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st) {
+    const RenderLaunch& L = B.r;
+    dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
+    const int smem = B.tf_in_smem ? L.tp.tf_w * L.tp.tf_h * 4 * (int)sizeof(float) : 0;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_render_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_render_backward<<<grid, 128, smem, st>>>(B);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

@@ -63,6 +63,15 @@ struct RenderLaunch {
     CamDev cams[kMaxCamsPerLaunch];
 };
 
+struct BackwardLaunch {
+    RenderLaunch r;
+    const float* dl_drgba;  // [n_cams][H][W][4] upstream gradient
+    float* dtf;             // [tf_h][tf_w][4], zeroed by the caller
+    float* dparams;         // gamma, ka, kd, ks, opacity_scale, zeroed by the caller
+    float* dvol;            // nvox or nullptr, zeroed by the caller
+    int tf_in_smem;         // 1: sum 1D transfer-function gradients in shared memory first
+};
+
 // ---------------------------------------------------------------- launchers
 // All return cudaSuccess or the launch error; all enqueue on `st`.
 cudaError_t launch_minmax_partials(const void* data, vr_dtype dt, long long n, float* partials, int nblocks,
@@ -85,6 +94,7 @@ cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas
                           float* tmp_b, float* smax, float* V, cudaStream_t st);
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
+cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
 int staged_smem_bytes(int warps_per_block, bool vessel);
 // Set the kernel's dynamic shared-memory limit and report resident CTAs per SM.

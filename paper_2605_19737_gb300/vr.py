@@ -70,6 +70,7 @@ SIGNATURES = {
     "vr_get_vesselness": ([_P, _I, _P, _I], _I),
     "vr_get_normalized": ([_P, _I, _P, _I], _I),
     "vr_render": ([_P, _I, _P, _I, _I, _I, _P, _I, ctypes.POINTER(vr_render_opts), _P, _P], _I),
+    "vr_render_backward": ([_P, _I, _P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(vr_render_opts)], _I),
 }
 
 _lib = None
