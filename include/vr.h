@@ -231,11 +231,51 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * |grad I|_max, the vesselness volume and each ray's stopping sample are
  * held fixed. Per ray the kernel re-marches forward, then sweeps back to front
  * rebuilding the transmittance by division (accurate while et_threshold stays
- * at or below ~0.999), re-evaluating each sample instead of storing it.
- * opts: NULL or as vr_render (only skip_empty is used). Errors as vr_render. */
+ * at or below ~0.999), re-evaluating each sample instead of storing it. The
+ * reverse sweep visits every sample, empty bricks included: a zero-opacity
+ * sample still gives the opacity entries it reads a gradient.
+ * opts: NULL or as vr_render (skip_empty applies to the forward re-march
+ * only, where it is exact). Errors as vr_render. */
 vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
                              const vr_render_opts* opts);
+
+/* ------------------------------------------------------- batched rendering */
+
+/* One view of a batch: a camera on a loaded volume, rendered into its own
+ * device image d_out ([H][W][4] float32, caller-owned). */
+typedef struct {
+    int vol_id;
+    vr_camera cam;
+    float* d_out;
+    int W, H;
+} vr_view;
+
+/* Register a batch of views (any mix of volumes, cameras and image sizes).
+ * The view table -- each volume's bricks, skip flags, transfer-function buffer
+ * and uniforms at this moment, plus the cameras and outputs -- is uploaded once
+ * to device memory (synchronises). Re-upload with vr_batch_update after
+ * vr_set_tissue_params; vr_free_volume of a member volume invalidates the
+ * batch. Errors: INVALID_ARG (unknown volume, bad size or output), NOT_READY
+ * (a volume without morphology or tissue params), OOM, CUDA. */
+vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* batch_id);
+vr_status vr_batch_update(vr_ctx* ctx, int batch_id);
+vr_status vr_batch_free(vr_ctx* ctx, int batch_id);
+
+/* Render every view of the batch in one persistent launch: warps pull
+ * 32-ray packets (opts->packet_w x 32/packet_w pixels, packet_w in {4, 8, 16, 32})
+ * from a single work queue spanning all views; opts->warps_per_block in [1, 8]
+ * (NULL opts: 8 x 4 packets, 8 warps per CTA). The grid is sized to the SMs
+ * times the resident CTAs per SM. Enqueues one memset and one kernel, with no
+ * host synchronisation or allocation, so it may be captured into a CUDA graph
+ * (capture of the legacy default stream is not possible). Results equal
+ * vr_render of each view bit for bit. */
+vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts, vr_counters* d_counters);
+
+/* As vr_batch_render, from a CUDA graph that the library captures once per
+ * (batch, packet shape, warps, skip) on a private stream and replays; ordered
+ * after earlier work on the context's stream and before later work. */
+vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts* opts);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,7 @@ from . import vr as _vr
 from .vr import (  # noqa: F401
     VR_F32, VR_U16, VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL,
     VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED,
-    vr_camera, vr_tissue_params, vr_counters, vr_render_opts,
+    vr_camera, vr_tissue_params, vr_counters, vr_render_opts, vr_view,
 )
 
 
@@ -225,6 +225,35 @@ class Context:
                                                  dparams.data_ptr(), dvol.data_ptr() if want_volume else None,
                                                  ctypes.byref(opts)))
         return dtf, dparams, (dvol if want_volume else None)
+
+
+    # -- batched rendering ----------------------------------------------------
+    def batch_create(self, views):
+        """views: iterable of (vol_id, camera (12,), out tensor (H, W, 4) on this device, W, H)."""
+        views = list(views)
+        arr = (vr_view * len(views))()
+        for k, (vol, cam, out, W, H) in enumerate(views):
+            c, _ = cameras_to_c(cam)
+            if not (out.is_cuda and out.is_contiguous() and tuple(out.shape[-3:]) == (H, W, 4)):
+                raise ValueError("view %d: output must be a contiguous (H, W, 4) device tensor" % k)
+            arr[k] = vr_view(int(vol), c[0], out.data_ptr(), int(W), int(H))
+        bid = ctypes.c_int()
+        self._check(self._lib.vr_batch_create(self._h, arr, len(views), ctypes.byref(bid)))
+        return bid.value
+
+    def batch_update(self, batch):
+        self._check(self._lib.vr_batch_update(self._h, batch))
+
+    def batch_free(self, batch):
+        self._check(self._lib.vr_batch_free(self._h, batch))
+
+    def batch_render(self, batch, packet_w=8, warps_per_block=8, skip_empty=True, counters=None, graph=False):
+        opts = vr_render_opts(VR_KERNEL_GATHER, int(bool(skip_empty)), int(packet_w), int(warps_per_block))
+        if graph:
+            self._check(self._lib.vr_batch_render_graph(self._h, batch, ctypes.byref(opts)))
+        else:
+            self._check(self._lib.vr_batch_render(self._h, batch, ctypes.byref(opts),
+                                                  counters.data_ptr() if counters is not None else None))
 
 
 def new_counters(device=0):

@@ -9,6 +9,8 @@
 
 #include <map>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "vr_async.cuh"
 #include "vr_internal.cuh"
@@ -39,6 +41,15 @@ struct Volume {
     bool morph_ready = false, params_ready = false;
 };
 
+struct Batch {
+    std::vector<vr_view> views;
+    std::vector<ViewDev> table;
+    ViewDev* d_views = nullptr;
+    int* d_prefix = nullptr;        // 4 packet shapes x n_views
+    int n_work[4] = {0, 0, 0, 0};   // packets per packet shape (packet_w = 4, 8, 16, 32)
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (packet_w, warps) -> graph
+};
+
 }  // namespace
 
 struct vr_ctx {
@@ -55,6 +66,11 @@ struct vr_ctx {
     size_t scratch_cap = 0;
     unsigned* d_work = nullptr;   // [0]: staged-kernel work counter, [1]: status word
     int staged_ctas[2][17] = {};   // resident CTAs per SM by (vesselness, warps per block)
+    int batch_ctas[17] = {};       // resident batch-kernel CTAs per SM by warps per block
+    std::map<int, Batch*> batches;
+    int next_batch = 1;
+    cudaStream_t graph_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 namespace {
@@ -191,7 +207,16 @@ vr_status vr_destroy(vr_ctx* ctx) {
     if (!ctx) return VR_OK;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->batches) {
+        for (auto& g : kv.second->graphs) cudaGraphExecDestroy(g.second);
+        cudaFree(kv.second->d_views);
+        cudaFree(kv.second->d_prefix);
+        delete kv.second;
+    }
     for (auto& kv : ctx->vols) free_volume(kv.second);
+    if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
     cudaFree(ctx->d_partials);
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_scratch);
@@ -591,6 +616,200 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         memcpy(B.r.cams, h_cams + c0, sizeof(CamDev) * nc);
         CK(launch_render_backward(B, ctx->stream), "render_backward kernel");
     }
+    return VR_OK;
+}
+
+namespace {
+
+int shape_index(int packet_w) { return packet_w == 4 ? 0 : packet_w == 8 ? 1 : packet_w == 16 ? 2 : packet_w == 32 ? 3 : -1; }
+
+// Refresh the device view table from the volumes' current state.
+vr_status batch_upload(vr_ctx* ctx, Batch* b) {
+    const int n = (int)b->views.size();
+    b->table.resize(n);
+    std::vector<int> prefix(4 * n);
+    for (int si = 0; si < 4; ++si) {
+        const int pw = 4 << si, ph = 32 / pw;
+        int acc = 0;
+        for (int i = 0; i < n; ++i) {
+            prefix[si * n + i] = acc;
+            acc += ((b->views[i].W + pw - 1) / pw) * ((b->views[i].H + ph - 1) / ph);
+        }
+        b->n_work[si] = acc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const vr_view& vw = b->views[i];
+        Volume* v = get_vol(ctx, vw.vol_id);
+        if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "batch: view %d names unknown volume %d", i, vw.vol_id);
+        if (!v->morph_ready || !v->params_ready)
+            return fail(ctx, VR_ERR_NOT_READY, "batch: volume %d lacks morphology or tissue params", vw.vol_id);
+        RenderLaunch L;
+        fill_launch(L, v, vw.W, vw.H, 1);
+        ViewDev& d = b->table[i];
+        d.vol = L.vol;
+        d.tp = L.tp;
+        d.tf = L.tf;
+        memcpy(&d.cam, &vw.cam, sizeof(CamDev));
+        d.out = vw.d_out;
+        d.W = vw.W;
+        d.H = vw.H;
+    }
+    CK(cudaMemcpyAsync(b->d_views, b->table.data(), sizeof(ViewDev) * n, cudaMemcpyHostToDevice, ctx->stream),
+       "batch: upload views");
+    CK(cudaMemcpyAsync(b->d_prefix, prefix.data(), sizeof(int) * 4 * n, cudaMemcpyHostToDevice, ctx->stream),
+       "batch: upload packet table");
+    CK(cudaStreamSynchronize(ctx->stream), "batch: upload sync");
+    return VR_OK;
+}
+
+// Enqueue one batched launch on `st` (no host synchronisation, no allocation).
+vr_status batch_enqueue(vr_ctx* ctx, Batch* b, const vr_render_opts& o, vr_counters* ctr, cudaStream_t st) {
+    const int si = shape_index(o.packet_w);
+    int& per_sm = ctx->batch_ctas[o.warps_per_block];
+    if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, &per_sm), "batch: occupancy");
+    if (per_sm < 1) return fail(ctx, VR_ERR_INVALID_ARG, "batch: kernel does not fit on an SM");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "batch: SM count");
+    BatchLaunch B;
+    memset(&B, 0, sizeof B);
+    B.views = b->d_views;
+    B.packet_prefix = b->d_prefix + si * (int)b->views.size();
+    B.n_views = (int)b->views.size();
+    B.n_work = b->n_work[si];
+    B.packet_w = o.packet_w;
+    B.packet_h = 32 / o.packet_w;
+    B.work_counter = ctx->d_work + 2;
+    B.counters = ctr;
+    B.skip = o.skip_empty ? 1 : 0;
+    const int need = (B.n_work + o.warps_per_block - 1) / o.warps_per_block;
+    int ctas = sms * per_sm;
+    if (ctas > need) ctas = need;
+    if (ctas < 1) ctas = 1;
+    CK(cudaMemsetAsync(ctx->d_work + 2, 0, sizeof(unsigned), st), "batch: reset work counter");
+    CK(launch_render_batch(B, o.warps_per_block, ctas, st), "batch kernel");
+    return VR_OK;
+}
+
+vr_status batch_opts(vr_ctx* ctx, const vr_render_opts* opts, vr_render_opts* o) {
+    *o = vr_render_opts{VR_KERNEL_AUTO, 1, 8, 8};
+    if (opts) *o = *opts;
+    if (shape_index(o->packet_w) < 0) return fail(ctx, VR_ERR_INVALID_ARG, "batch: packet_w must be 4, 8, 16 or 32");
+    if (o->warps_per_block < 1 || o->warps_per_block > 8)
+        return fail(ctx, VR_ERR_INVALID_ARG, "batch: warps_per_block must be in [1, 8]");
+    return VR_OK;
+}
+
+}  // namespace
+
+vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* batch_id) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!views || !batch_id || n_views < 1 || n_views > (1 << 20))
+        return fail(ctx, VR_ERR_INVALID_ARG, "batch_create: bad arguments");
+    long long packets = 0;
+    for (int i = 0; i < n_views; ++i) {
+        if (!views[i].d_out || views[i].W < 1 || views[i].H < 1 || views[i].W > 16384 || views[i].H > 16384)
+            return fail(ctx, VR_ERR_INVALID_ARG, "batch_create: view %d has a bad output or size", i);
+        packets += ((long long)(views[i].W + 3) / 4) * ((views[i].H + 7) / 8);
+    }
+    if (packets >= (1LL << 31)) return fail(ctx, VR_ERR_INVALID_ARG, "batch_create: too many rays");
+    DeviceGuard g(ctx->device);
+    Batch* b = new Batch();
+    b->views.assign(views, views + n_views);
+    cudaError_t e = dalloc(&b->d_views, sizeof(ViewDev) * n_views);
+    if (e == cudaSuccess) e = dalloc(&b->d_prefix, sizeof(int) * 4 * n_views);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_views);
+        delete b;
+        return cuda_fail(ctx, e, "batch_create: allocate");
+    }
+    vr_status st = batch_upload(ctx, b);
+    if (st != VR_OK) {
+        cudaFree(b->d_views);
+        cudaFree(b->d_prefix);
+        delete b;
+        return st;
+    }
+    const int id = ctx->next_batch++;
+    ctx->batches[id] = b;
+    *batch_id = id;
+    return VR_OK;
+}
+
+vr_status vr_batch_update(vr_ctx* ctx, int batch_id) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    auto it = ctx->batches.find(batch_id);
+    if (it == ctx->batches.end()) return fail(ctx, VR_ERR_INVALID_ARG, "batch_update: unknown batch %d", batch_id);
+    DeviceGuard g(ctx->device);
+    return batch_upload(ctx, it->second);
+}
+
+vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts, vr_counters* d_counters) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    auto it = ctx->batches.find(batch_id);
+    if (it == ctx->batches.end()) return fail(ctx, VR_ERR_INVALID_ARG, "batch_render: unknown batch %d", batch_id);
+    vr_render_opts o;
+    vr_status st = batch_opts(ctx, opts, &o);
+    if (st != VR_OK) return st;
+    DeviceGuard g(ctx->device);
+    return batch_enqueue(ctx, it->second, o, d_counters, ctx->stream);
+}
+
+vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts* opts) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    auto it = ctx->batches.find(batch_id);
+    if (it == ctx->batches.end())
+        return fail(ctx, VR_ERR_INVALID_ARG, "batch_render_graph: unknown batch %d", batch_id);
+    vr_render_opts o;
+    vr_status st = batch_opts(ctx, opts, &o);
+    if (st != VR_OK) return st;
+    DeviceGuard g(ctx->device);
+    Batch* b = it->second;
+    if (!ctx->graph_stream) {
+        CK(cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking), "graph stream");
+        CK(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming), "graph event");
+        CK(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming), "graph event");
+    }
+    const auto key = std::make_pair(o.packet_w, o.warps_per_block * 2 + (o.skip_empty ? 1 : 0));
+    auto git = b->graphs.find(key);
+    if (git == b->graphs.end()) {
+        // occupancy and SM count are queried outside the capture
+        int& per_sm = ctx->batch_ctas[o.warps_per_block];
+        if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, &per_sm), "batch: occupancy");
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+        vr_status es = batch_enqueue(ctx, b, o, nullptr, ctx->graph_stream);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->graph_stream, &graph);
+        if (es != VR_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return es;
+        }
+        CK(e2, "graph capture end");
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e3, "graph instantiate");
+        git = b->graphs.emplace(key, exec).first;
+    }
+    CK(cudaEventRecord(ctx->ev_in, ctx->stream), "graph fence in");
+    CK(cudaStreamWaitEvent(ctx->graph_stream, ctx->ev_in, 0), "graph fence in wait");
+    CK(cudaGraphLaunch(git->second, ctx->graph_stream), "graph launch");
+    CK(cudaEventRecord(ctx->ev_out, ctx->graph_stream), "graph fence out");
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out, 0), "graph fence out wait");
+    return VR_OK;
+}
+
+vr_status vr_batch_free(vr_ctx* ctx, int batch_id) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    auto it = ctx->batches.find(batch_id);
+    if (it == ctx->batches.end()) return fail(ctx, VR_ERR_INVALID_ARG, "batch_free: unknown batch %d", batch_id);
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph_stream) cudaStreamSynchronize(ctx->graph_stream);
+    for (auto& gx : it->second->graphs) cudaGraphExecDestroy(gx.second);
+    cudaFree(it->second->d_views);
+    cudaFree(it->second->d_prefix);
+    delete it->second;
+    ctx->batches.erase(it);
     return VR_OK;
 }
 

@@ -3,10 +3,12 @@
 // (gamma, ka, kd, ks, opacity_scale) and the normalised voxel intensities.
 //
 // One thread per ray (the forward kernel's 8x4 warp packets). Per ray:
-//   1. forward re-march with the forward kernel's exact arithmetic, recording the
-//      stopping sample k_stop and the transmittance T before it;
-//   2. reverse sweep k = k_stop .. 0 with no stored samples: the sample is
-//      re-evaluated, T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and
+//   1. forward re-march with the forward kernel's exact arithmetic (empty bricks
+//      skipped), recording the stopping sample k_stop and the transmittance T
+//      before it;
+//   2. reverse sweep over every sample k = k_stop .. 0 (no skipping: the opacity
+//      entries of the transfer function receive gradient from samples whose
+//      opacity is zero) with no stored samples: the sample is re-evaluated, T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and
 //      well conditioned because early termination keeps 1 - alpha_k >= 1 - et
 //      before the last sample), R_k = alpha_k c_k + (1 - alpha_k) R_{k+1} and
 //      P_k = prod_{j>k} (1 - alpha_j) are carried backwards, and
@@ -108,8 +110,9 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
                     sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
                     bc[q] = i0[q] >> 3;
                 }
+                // No skipping here: a sample in an empty brick has alpha = 0, but its lookup
+                // still gives the opacity entries it reads a non-zero gradient.
                 const long long bi = bidx(v, bc);
-                if (L.skip && __ldg(v.empty + bi)) continue;  // alpha = 0: T, R, P unchanged
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
                 float fld[10];

@@ -72,6 +72,26 @@ struct BackwardLaunch {
     int tf_in_smem;         // 1: sum 1D transfer-function gradients in shared memory first
 };
 
+// One view of a batched render (device-resident table).
+struct ViewDev {
+    VolumeDev vol;
+    TissueDev tp;
+    const float* tf;
+    CamDev cam;
+    float* out;     // [H][W][4]
+    int W, H;
+};
+
+struct BatchLaunch {
+    const ViewDev* views;
+    const int* packet_prefix;  // n_views entries: first packet of each view
+    int n_views, n_work;
+    int packet_w, packet_h;
+    unsigned* work_counter;    // zeroed before every launch
+    vr_counters* counters;     // nullable
+    int skip;
+};
+
 // ---------------------------------------------------------------- launchers
 // All return cudaSuccess or the launch error; all enqueue on `st`.
 cudaError_t launch_minmax_partials(const void* data, vr_dtype dt, long long n, float* partials, int nblocks,
@@ -95,6 +115,8 @@ cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
 cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st);
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st);
+cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
 int staged_smem_bytes(int warps_per_block, bool vessel);
 // Set the kernel's dynamic shared-memory limit and report resident CTAs per SM.

@@ -36,6 +36,54 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
     }
 }
 
+// Front-to-back march of one ray (Eqs. 4-6) over the bricked volume in HBM/L2,
+// skipping bricks classified empty. Shared by the single-view and batched kernels.
+__device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
+                                             const RayDev& r, int skip, float inv_gmax, const float is[3],
+                                             float4& out, unsigned& dense, unsigned& evald) {
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    int k = 0, kstop = -1;
+    unsigned ne = 0;
+    while (k < r.ns) {
+        const float kk = (float)k + 0.5f;
+        int i0[3], bc[3];
+        float f[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+            bc[q] = i0[q] >> 3;
+        }
+        const long long bi = brick_index(v, bc);
+        if (skip && __ldg(v.empty + bi)) {
+            k = brick_exit_k(r, bc, k, r.ns);
+            continue;
+        }
+        const int base =
+            ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge + (i0[0] - kCells * bc[0]);
+        const long long boff = bi * kBrickVox;
+        float fld[10];
+        field_eval(GlobalLoad{v.bricks + boff}, base, f[0], f[1], f[2], fld);
+        scale_field(fld, is);
+        const float vval = v.vbricks ? value_eval(GlobalLoad{v.vbricks + boff}, base, f[0], f[1], f[2]) : 0.0f;
+        float alpha, col[3];
+        sample_optics(fld, vval, r.dir, tp, tf, inv_gmax, alpha, col);
+        const float wgt = (1.0f - A) * alpha;  // Eqs. 5-6
+        C0 = fmaf(col[0], wgt, C0);
+        C1 = fmaf(col[1], wgt, C1);
+        C2 = fmaf(col[2], wgt, C2);
+        A += wgt;
+        ++ne;
+        if (A >= tp.et_threshold) {
+            kstop = k;
+            break;
+        }
+        ++k;
+    }
+    out = make_float4(C0, C1, C2, A);
+    dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;
+    evald = ne;
+}
+
 __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
@@ -50,50 +98,12 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
 
     RayDev r;
     const bool hit = inside && setup_ray(L.cams[cam], L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned dense = 0, evald = 0;
-    if (hit) {
-        int k = 0, kstop = -1;
-        while (k < r.ns) {
-            const float kk = (float)k + 0.5f;
-            int i0[3], bc[3];
-            float f[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
-                bc[q] = i0[q] >> 3;
-            }
-            const long long bi = brick_index(v, bc);
-            if (L.skip && __ldg(v.empty + bi)) {
-                k = brick_exit_k(r, bc, k, r.ns);
-                continue;
-            }
-            const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
-                             (i0[0] - kCells * bc[0]);
-            const long long boff = bi * kBrickVox;
-            float fld[10];
-            field_eval(GlobalLoad{v.bricks + boff}, base, f[0], f[1], f[2], fld);
-            scale_field(fld, is);
-            const float vval = v.vbricks ? value_eval(GlobalLoad{v.vbricks + boff}, base, f[0], f[1], f[2]) : 0.0f;
-            float alpha, col[3];
-            sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
-            const float wgt = (1.0f - A) * alpha;  // Eqs. 5-6
-            C0 = fmaf(col[0], wgt, C0);
-            C1 = fmaf(col[1], wgt, C1);
-            C2 = fmaf(col[2], wgt, C2);
-            A += wgt;
-            ++evald;
-            if (A >= L.tp.et_threshold) {
-                kstop = k;
-                break;
-            }
-            ++k;
-        }
-        dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;
-    }
+    if (hit) march_gather(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
-        reinterpret_cast<float4*>(L.out)[pix] = make_float4(C0, C1, C2, A);
+        reinterpret_cast<float4*>(L.out)[pix] = px;
         if (L.ray_samples) {
             L.ray_samples[2 * pix] = dense;
             L.ray_samples[2 * pix + 1] = evald;
@@ -102,11 +112,63 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
     if (L.counters) add_counters(L.counters, hit ? 1u : 0u, dense, evald, 0u);
 }
 
+// Batched persistent renderer: every warp pulls packet_w x packet_h ray packets
+// from one work queue spanning all views (each view: its own volume, uniforms,
+// transfer function, camera, output and size). A packet's view is found by
+// binary search over the views' packet prefix sums.
+__global__ void __launch_bounds__(256) k_render_batch(const __grid_constant__ BatchLaunch B) {
+    const int lane = threadIdx.x & 31;
+    unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0;
+    while (true) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(B.work_counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned)B.n_work) break;
+        int lo = 0, hi = B.n_views - 1;  // last view with prefix <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned)__ldg(B.packet_prefix + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev& vw = B.views[lo];
+        const int local = (int)item - __ldg(B.packet_prefix + lo);
+        const int npx = (vw.W + B.packet_w - 1) / B.packet_w;
+        const int px = local % npx, py = local / npx;
+        const int i = px * B.packet_w + lane % B.packet_w, j = py * B.packet_h + lane / B.packet_w;
+        const bool inside = i < vw.W && j < vw.H;
+        const VolumeDev& v = vw.vol;
+        const float gmax = __ldg(&v.vc->gmax);
+        const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+        const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
+        RayDev r;
+        const bool hit = inside && setup_ray(vw.cam, vw.W, vw.H, i, j, v.n, v.s, vw.tp.step_vox, r);
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned dense = 0, evald = 0;
+        if (hit)
+            march_gather(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out, dense,
+                         evald);
+        if (inside) reinterpret_cast<float4*>(vw.out)[(long long)j * vw.W + i] = out;
+        rays_hit += hit ? 1u : 0u;
+        dense_tot += dense;
+        eval_tot += evald;
+    }
+    if (B.counters) add_counters(B.counters, rays_hit, dense_tot, eval_tot, 0u);
+}
+
 }  // namespace
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st) {
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
     k_render_gather<<<grid, 128, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch, warps_per_block * 32, 0);
+}
+
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st) {
+    k_render_batch<<<ctas, warps_per_block * 32, 0, st>>>(B);
     return cudaGetLastError();
 }
 

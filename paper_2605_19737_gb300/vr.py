@@ -40,6 +40,11 @@ class vr_counters(ctypes.Structure):
                 ("evaluated_samples", ctypes.c_ulonglong), ("bricks_staged", ctypes.c_ulonglong)]
 
 
+class vr_view(ctypes.Structure):
+    _fields_ = [("vol_id", ctypes.c_int), ("cam", vr_camera), ("d_out", ctypes.c_void_p), ("W", ctypes.c_int),
+                ("H", ctypes.c_int)]
+
+
 class vr_render_opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("skip_empty", ctypes.c_int), ("packet_w", ctypes.c_int),
                 ("warps_per_block", ctypes.c_int)]
@@ -70,6 +75,11 @@ SIGNATURES = {
     "vr_get_vesselness": ([_P, _I, _P, _I], _I),
     "vr_get_normalized": ([_P, _I, _P, _I], _I),
     "vr_render": ([_P, _I, _P, _I, _I, _I, _P, _I, ctypes.POINTER(vr_render_opts), _P, _P], _I),
+    "vr_batch_create": ([_P, _P, _I, ctypes.POINTER(_I)], _I),
+    "vr_batch_update": ([_P, _I], _I),
+    "vr_batch_free": ([_P, _I], _I),
+    "vr_batch_render": ([_P, _I, ctypes.POINTER(vr_render_opts), _P], _I),
+    "vr_batch_render_graph": ([_P, _I, ctypes.POINTER(vr_render_opts)], _I),
     "vr_render_backward": ([_P, _I, _P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(vr_render_opts)], _I),
 }
 
