@@ -136,6 +136,69 @@ def run_reference(args):
                                             "d2h_bytes_per_step": 0}})
 
 
+def run_batched(args, ctx, dev, flush):
+    """Four uneven volumes x 64 orbit cameras at 512x512 in one persistent launch,
+    replayed from a CUDA graph with the autotuned packet shape, beside the same 256
+    views rendered one vr_render call at a time."""
+    import torch
+
+    import paper_2605_19737_gb300 as pkg
+    from paper_2605_19737_gb300 import autotune
+    from phantoms import workloads
+
+    cases = workloads.batched_4vol_64cam()
+    vids, views = [], []
+    for case in cases:
+        vid = ctx.load_volume(torch.from_numpy(case["volume"]).to(dev), case["spacing"])
+        ctx.precompute_morphology(vid)
+        ctx.set_tissue_params(vid, case["tf"], **case["params"])
+        vids.append(vid)
+        for c in range(case["cams"].shape[0]):
+            out = torch.empty((case["H"], case["W"], 4), device=dev)
+            views.append((vid, case["cams"][c], out, case["W"], case["H"]))
+    bid = ctx.batch_create(views)
+    tune = autotune.tune_batch(ctx, bid, "batched_4vol_64cam_512", reps=2, force=True,
+                               candidates=[(pw, w) for pw in (4, 8, 16) for w in (4, 8)])
+    pw, wpb = tune["packet_w"], tune["warps_per_block"]
+    ctr = pkg.new_counters(dev.index)
+    ctx.batch_render(bid, packet_w=pw, warps_per_block=wpb, counters=ctr)
+    torch.cuda.synchronize()
+    dense = int(ctr[1])
+    for _ in range(args.warmup):
+        ctx.batch_render(bid, packet_w=pw, warps_per_block=wpb, graph=True)
+    ts = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        ctx.batch_render(bid, packet_w=pw, warps_per_block=wpb, graph=True)
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    batch_ms = float(np.mean(ts))
+    single = []
+    for _ in range(2):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for vid, cam, out, W, H in views:
+            ctx.render(vid, cam, W, H, out=out.view(1, H, W, 4))
+        e.record()
+        torch.cuda.synchronize()
+        single.append(s.elapsed_time(e))
+    single_ms = float(np.min(single))
+    ctx.batch_free(bid)
+    for vid in vids:
+        ctx.free_volume(vid)
+    return {"workload": "batched_4vol_64cam: 96^3, 128x160x128, 181x217x181, 256x256x176 float32; "
+                        "64 orbit cameras each; 512x512", "views": len(views), "dense_samples": dense,
+            "gsamples_per_s": dense / (batch_ms * 1e-3) / 1e9, "ms_per_batch": batch_ms,
+            "launch": "one persistent kernel from a CUDA graph", "autotuned": {"packet_w": pw,
+                                                                               "warps_per_block": wpb,
+                                                                               "timings_ms": tune["timings"]},
+            "single_view_gsamples_per_s": dense / (single_ms * 1e-3) / 1e9, "single_view_ms": single_ms}
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -229,6 +292,34 @@ def run(args):
         e2e_s = float(t.item())
     e2e_value = dense_all / e2e_s / 1e9
 
+    # Forward + backward on the same view: dL/dRGBA is a fixed seeded upstream gradient;
+    # the backward returns transfer-function, uniform and voxel gradients.
+    fwd_bwd = None
+    if not args.no_backward:
+        g = torch.Generator(device=dev).manual_seed(20260519)
+        dl = torch.randn((1, H, W, 4), device=dev, generator=g)
+        dtf = torch.empty(tuple(case["tf"].shape), device=dev)
+        dpar = torch.empty(5, device=dev)
+        dvol = torch.empty(vol_np.shape, device=dev)
+        fb = []
+        for i in range(args.warmup + max(3, args.steps // 4)):
+            flush.zero_()
+            s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            s0.record()
+            frame()
+            s1.record()
+            ctx.render_backward(vid, case["cams"], W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol)
+            s2.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                fb.append((s0.elapsed_time(s1), s1.elapsed_time(s2)))
+        f_ms, b_ms = (float(np.mean([x[q] for x in fb])) for q in (0, 1))
+        fwd_bwd = {"gsamples_per_s": dense_all / ((f_ms + b_ms) * 1e-3) / 1e9, "ms_per_step": f_ms + b_ms,
+                   "fwd_ms": f_ms, "bwd_ms": b_ms, "fps": 1000.0 / (f_ms + b_ms),
+                   "grads": "transfer function 256x64x4, 5 uniforms, 181x217x181 voxels",
+                   "plain_fwd_gsamples_per_s": value}
+
+    batched = None if args.no_batch else run_batched(args, ctx, dev, flush)
     hbm, smax, peak_kind = _peaks()
     nbricks = int(np.prod([(n - 1 + 7) // 8 for n in vol_np.shape]))
     frame_bytes = nbricks * 6912 + W * H * 16
@@ -261,7 +352,9 @@ def run(args):
                              "peak_source": peak_kind},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tf_host.nbytes + 48),
                     "d2h_bytes_per_step": int(W * H * 16), "ms_per_step": 1000.0 * e2e_s},
-            "gpu_launches": args.steps,
+            "fwd_bwd": fwd_bwd,
+            "batched": batched,
+            "gpu_launches": args.steps,  # one raymarch kernel per timed frame
             "clocks": clk,
             "cpu_baseline": cb,
         })
@@ -278,6 +371,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="gather", choices=["staged", "gather"])
+    ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -570,8 +570,8 @@ int or_render_brute(const double *In, const int *n, const double *s, const or_pa
  * qlo = floor(min * 65535), qhi = ceil(max * 65535). The normalisation and the
  * quantisation are taken in IEEE float32 with round-to-nearest, one operation at
  * a time (d = x - imin; r = d / (imax - imin); r * 65535), because these floats
- * decide integers that must match the kernel's bit for bit. raw holds float32
- * or uint16 values; grid is [nbz][nby][nbx][2]. */
+ * decide integers that must match the kernel's bit for bit; codes are clamped to
+ * [0, 65535]. raw holds float32 or uint16 values; grid is [nbz][nby][nbx][2]. */
 void or_brick_minmax_q(const float *raw, const int *n, float imin, float imax, uint16_t *grid) {
     int nb[3];
     for (int a = 0; a < 3; ++a) nb[a] = (n[a] - 1 + 7) / 8;
@@ -590,8 +590,8 @@ void or_brick_minmax_q(const float *raw, const int *n, float imin, float imax, u
                         }
                 volatile float ql = lo * 65535.0f, qh = hi * 65535.0f;
                 int64_t b = ((int64_t)bz * nb[1] + by) * nb[0] + bx;
-                grid[2 * b + 0] = (uint16_t)floorf(ql);
-                grid[2 * b + 1] = (uint16_t)ceilf(qh);
+                grid[2 * b + 0] = (uint16_t)fminf(fmaxf(floorf(ql), 0.0f), 65535.0f);
+                grid[2 * b + 1] = (uint16_t)fminf(fmaxf(ceilf(qh), 0.0f), 65535.0f);
             }
 }
 

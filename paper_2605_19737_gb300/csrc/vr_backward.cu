@@ -8,8 +8,9 @@
 //      before it;
 //   2. reverse sweep over every sample k = k_stop .. 0 (no skipping: the opacity
 //      entries of the transfer function receive gradient from samples whose
-//      opacity is zero) with no stored samples: the sample is re-evaluated, T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and
-//      well conditioned because early termination keeps 1 - alpha_k >= 1 - et
+//      opacity is zero) with no stored samples: the sample is re-evaluated,
+//      T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and well
+//      conditioned because early termination keeps 1 - alpha_k >= 1 - et
 //      before the last sample), R_k = alpha_k c_k + (1 - alpha_k) R_{k+1} and
 //      P_k = prod_{j>k} (1 - alpha_j) are carried backwards, and
 //        dL/dalpha_k = T_k (<dL/dC, c_k - R_{k+1}> + dL/dA P_k),
@@ -95,8 +96,8 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
             }
             ++k;
         }
-        if (klast >= 0) {
-            // transmittance before the stopping sample
+        {
+            // transmittance before the stopping sample (1 when no sample had opacity)
             float Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
             float Tk1 = Tk, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;
             const float dC[3] = {g4.x, g4.y, g4.z};

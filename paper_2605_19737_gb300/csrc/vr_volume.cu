@@ -175,8 +175,10 @@ __global__ void __launch_bounds__(256) k_brick_minmax(const float* __restrict__ 
     }
     warp_minmax(lo, hi);
     if (lane == 0) {
-        grid[2 * b] = (uint16_t)floorf(__fmul_rn(lo, 65535.0f));
-        grid[2 * b + 1] = (uint16_t)ceilf(__fmul_rn(hi, 65535.0f));
+        // codes clamp to [0, 65535]: intensities set outside [0, 1] (vr_set_normalized)
+        // look up the transfer function's end entries, which the clamped range covers
+        grid[2 * b] = (uint16_t)fminf(fmaxf(floorf(__fmul_rn(lo, 65535.0f)), 0.0f), 65535.0f);
+        grid[2 * b + 1] = (uint16_t)fminf(fmaxf(ceilf(__fmul_rn(hi, 65535.0f)), 0.0f), 65535.0f);
     }
 }
 
