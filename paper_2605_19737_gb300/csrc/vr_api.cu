@@ -64,6 +64,8 @@ struct vr_ctx {
     size_t stage_cap = 0;
     float* d_scratch = nullptr;   // vesselness smoothing scratch (2 volumes)
     size_t scratch_cap = 0;
+    float* d_tfgrad = nullptr;    // private copies of a 2D transfer-function gradient
+    size_t tfgrad_cap = 0;
     unsigned* d_work = nullptr;   // [0]: staged-kernel work counter, [1]: status word
     int staged_ctas[2][17] = {};   // resident CTAs per SM by (vesselness, warps per block)
     int batch_ctas[17] = {};       // resident batch-kernel CTAs per SM by warps per block
@@ -220,6 +222,7 @@ vr_status vr_destroy(vr_ctx* ctx) {
     cudaFree(ctx->d_partials);
     cudaFree(ctx->d_stage);
     cudaFree(ctx->d_scratch);
+    cudaFree(ctx->d_tfgrad);
     cudaFree(ctx->d_work);
     (void)cudaGetLastError();
     delete ctx;
@@ -609,6 +612,20 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     B.dparams = d_dparams;
     B.dvol = d_dvolume;
     B.tf_in_smem = (v->tp.tf_h == 1 && ntf * sizeof(float) <= 64 * 1024) ? 1 : 0;
+    if (!B.tf_in_smem) {
+        const size_t need = sizeof(float) * ntf * kTfGradCopies;
+        if (ctx->tfgrad_cap < need) {
+            CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
+            cudaFree(ctx->d_tfgrad);
+            ctx->d_tfgrad = nullptr;
+            ctx->tfgrad_cap = 0;
+            CK(dalloc(&ctx->d_tfgrad, need), "render_backward: transfer-function gradient scratch");
+            ctx->tfgrad_cap = need;
+        }
+        CK(cudaMemsetAsync(ctx->d_tfgrad, 0, need, ctx->stream), "render_backward: zero scratch");
+        B.dtf_copies = ctx->d_tfgrad;
+        B.n_copies = kTfGradCopies;
+    }
     for (int c0 = 0; c0 < n_cams; c0 += kMaxCamsPerLaunch) {
         const int nc = n_cams - c0 < kMaxCamsPerLaunch ? n_cams - c0 : kMaxCamsPerLaunch;
         B.r.n_cams = nc;
@@ -616,6 +633,9 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         memcpy(B.r.cams, h_cams + c0, sizeof(CamDev) * nc);
         CK(launch_render_backward(B, ctx->stream), "render_backward kernel");
     }
+    if (!B.tf_in_smem)
+        CK(launch_sum_copies(ctx->d_tfgrad, kTfGradCopies, (long long)ntf, d_dtf, ctx->stream),
+           "render_backward: sum gradient copies");
     return VR_OK;
 }
 

@@ -17,8 +17,10 @@
 //        dL/dc_k     = T_k alpha_k dL/dC              (Eqs. 5-6 differentiated);
 //   3. sample_adjoint / field_adjoint_scatter chain these to the parameters.
 // Transfer-function gradients of a 1D table are summed in shared memory per CTA
-// and flushed with one atomic per non-zero entry; 2D tables and voxels use
-// global atomics; uniform gradients are warp-reduced first.
+// and flushed with one atomic per non-zero entry; a 2D table is summed into 64
+// private global copies (CTA c into copy c % 64) that k_sum_copies adds up
+// afterwards -- contended atomics on one 256 KB table cost 10x the rest of the
+// kernel; voxels use global atomics; uniform gradients are warp-reduced first.
 #include "vr_adjoint.cuh"
 
 namespace vr {
@@ -42,7 +44,12 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
         for (int e = threadIdx.x; e < ntf; e += blockDim.x) s_dtf[e] = 0.0f;
         __syncthreads();
     }
-    const TfGradSink sink{B.tf_in_smem ? s_dtf : B.dtf};
+    // 1D tables: one shared-memory copy per CTA. 2D tables (too large for shared
+    // memory): one of n_copies private global copies, so that CTAs working on the
+    // same hot entries do not serialise on one address.
+    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
+    const TfGradSink sink{tf_dst};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
@@ -168,7 +175,23 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
     }
 }
 
+// dtf[e] = sum of the n_copies private copies of entry e.
+__global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ copies, int n_copies, long long n,
+                                                   float* __restrict__ out) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int c = 0; c < n_copies; ++c) acc += __ldg(copies + (size_t)c * n + e);
+        out[e] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st) {
+    const long long blocks = (n + 255) / 256;
+    k_sum_copies<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(copies, n_copies, n, dtf);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st) {
     const RenderLaunch& L = B.r;

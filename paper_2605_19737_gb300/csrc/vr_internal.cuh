@@ -70,7 +70,11 @@ struct BackwardLaunch {
     float* dparams;         // gamma, ka, kd, ks, opacity_scale, zeroed by the caller
     float* dvol;            // nvox or nullptr, zeroed by the caller
     int tf_in_smem;         // 1: sum 1D transfer-function gradients in shared memory first
+    float* dtf_copies;      // else: n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
+    int n_copies;
 };
+
+constexpr int kTfGradCopies = 64;
 
 // One view of a batched render (device-resident table).
 struct ViewDev {
@@ -115,6 +119,8 @@ cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
 cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st);
+// dtf[e] = sum over c of copies[c * n + e]
+cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st);
 cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
