@@ -240,6 +240,30 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
                              const vr_render_opts* opts);
 
+/* Allocation-free variant of the brick classification that vr_set_tissue_params
+ * runs. The paper has no counterpart; it exists for callers that cannot allocate
+ * device memory when they re-classify (a fixed pre-reserved memory budget, a
+ * real-time thread that must stay out of the allocator). No context is needed and
+ * nothing is allocated: the kernels' scratch (tf_w + 1 prefix counts) lives in a
+ * 16 KB static device array built into the library, which every GPU that loads
+ * the library holds until the process exits.
+ *   d_grid:  nbricks x (qlo, qhi) uint16, as vr_get_bricks returns (device);
+ *   d_tf:    [tf_h][tf_w][4] float32 transfer function (device);
+ *   d_empty: nbricks bytes out, 1 = brick skippable (device), identical to the
+ *            flags vr_set_tissue_params computes for the same grid and table;
+ *   cuda_stream: stream to enqueue on (NULL = legacy default stream), on the
+ *            current CUDA device;
+ *   h_msg/msg_len: NULL or a host buffer that receives a message on failure.
+ * The first call on a device looks up the static array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array per device, so calls that overlap on the GPU
+ * (e.g. on two streams) race; every call rewrites all the entries it reads.
+ * Errors: INVALID_ARG (NULL pointers, nbricks outside [1, 2^31], tf_w outside
+ * [2, 4096] -- the most the static scratch holds -- or tf_h outside [1, 256]),
+ * CUDA. Asynchronous otherwise. */
+vr_status vr_classify_bricks_noalloc(const unsigned short* d_grid, long long nbricks, const float* d_tf, int tf_w,
+                                     int tf_h, unsigned char* d_empty, void* cuda_stream, char* h_msg, int msg_len);
+
 /* ------------------------------------------------------- batched rendering */
 
 /* One view of a batch: a camera on a loaded volume, rendered into its own

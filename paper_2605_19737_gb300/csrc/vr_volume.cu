@@ -308,3 +308,91 @@ cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float
 }
 
 }  // namespace vr
+
+// ---------------------------------------------------------------------------
+// Allocation-free brick classification.
+//
+// Some callers cannot allocate device memory at the point where they need to
+// re-classify bricks: a host that hands the GPU to this library with a fixed,
+// pre-reserved memory budget, a real-time interaction thread that must not
+// enter the allocator, or code running while another component holds the
+// device's allocator. For them this entry point runs the same two kernels as
+// vr_set_tissue_params' classification, but keeps their scratch (the
+// transfer-function column prefix table) in a static device array compiled into
+// the library instead of asking for memory.
+#include <mutex>
+
+namespace vr {
+namespace {
+
+constexpr int kStaticTfMaxW = 4096;  // largest table width the static scratch holds
+constexpr int kStaticMaxDevices = 64;
+
+// tf_w + 1 prefix counts; every call rewrites all the entries it reads, so
+// nothing here has to start at zero. Each GPU that loads the library holds
+// these 16 KB until the process exits.
+static __device__ __align__(256) int g_static_prefix[kStaticTfMaxW + 1];
+
+std::mutex g_static_mu;
+int* g_static_prefix_ptr[kStaticMaxDevices] = {};
+
+void put_msg(char* buf, int len, const char* msg) {
+    if (!buf || len <= 0) return;
+    int i = 0;
+    for (; i < len - 1 && msg[i]; ++i) buf[i] = msg[i];
+    buf[i] = '\0';
+}
+
+}  // namespace
+}  // namespace vr
+
+extern "C" vr_status vr_classify_bricks_noalloc(const unsigned short* d_grid, long long nbricks, const float* d_tf,
+                                                int tf_w, int tf_h, unsigned char* d_empty, void* cuda_stream,
+                                                char* h_msg, int msg_len) {
+    using namespace vr;
+    put_msg(h_msg, msg_len, "");
+    if (!d_grid || !d_tf || !d_empty || nbricks < 1 || nbricks > (1LL << 31)) {
+        put_msg(h_msg, msg_len, "classify_bricks_noalloc: NULL pointer or brick count outside [1, 2^31]");
+        return VR_ERR_INVALID_ARG;
+    }
+    if (tf_w < 2 || tf_w > kStaticTfMaxW) {
+        put_msg(h_msg, msg_len,
+                "classify_bricks_noalloc: tf_w must be in [2, 4096]; the static scratch holds 4097 prefix counts");
+        return VR_ERR_INVALID_ARG;
+    }
+    if (tf_h < 1 || tf_h > 256) {
+        put_msg(h_msg, msg_len, "classify_bricks_noalloc: tf_h must be in [1, 256]");
+        return VR_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+        (void)cudaGetLastError();
+        put_msg(h_msg, msg_len, "classify_bricks_noalloc: no usable current CUDA device");
+        return VR_ERR_CUDA;
+    }
+    int* prefix = nullptr;
+    {
+        // once per device, with that device current: the device address of the
+        // static array (the host-side symbol is not a device pointer)
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_prefix_ptr[dev]) {
+            int* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_prefix);
+            if (e != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                put_msg(h_msg, msg_len, "classify_bricks_noalloc: cudaGetSymbolAddress of the static scratch failed");
+                return VR_ERR_CUDA;
+            }
+            g_static_prefix_ptr[dev] = p;
+        }
+        prefix = g_static_prefix_ptr[dev];
+    }
+    const cudaError_t e = launch_classify(reinterpret_cast<const uint16_t*>(d_grid), nbricks, d_tf, tf_w, tf_h,
+                                          reinterpret_cast<uint8_t*>(d_empty), prefix, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        put_msg(h_msg, msg_len, cudaGetErrorString(e));
+        return VR_ERR_CUDA;
+    }
+    return VR_OK;
+}
