@@ -44,6 +44,11 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
     int k = 0, kstop = -1;
     unsigned ne = 0;
+    // The skip flag of the current brick is re-read only when the brick changes
+    // (about every 16 samples), keeping a dependent L1 round trip off the path of
+    // every sample.
+    long long flag_bi = -1;
+    bool flag_empty = false;
     while (k < r.ns) {
         const float kk = (float)k + 0.5f;
         int i0[3], bc[3];
@@ -54,7 +59,11 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             bc[q] = i0[q] >> 3;
         }
         const long long bi = brick_index(v, bc);
-        if (skip && __ldg(v.empty + bi)) {
+        if (skip && bi != flag_bi) {
+            flag_bi = bi;
+            flag_empty = __ldg(v.empty + bi) != 0;
+        }
+        if (skip && flag_empty) {
             k = brick_exit_k(r, bc, k, r.ns);
             continue;
         }
