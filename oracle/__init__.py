@@ -77,6 +77,9 @@ def _load():
         L.or_frangi.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]
         L.or_render_grad.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+        L.or_histogram256.argtypes = [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P]
+        L.or_tissue_peaks.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+        L.or_tissue_peaks.restype = ctypes.c_int
         L.or_sample_points.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P,
                                        ctypes.c_int64, _P, _P]
     return _lib
@@ -282,6 +285,27 @@ def classify(grid, tf):
     out = np.zeros(g.shape[:-1], np.uint8)
     L.or_classify(_ptr(g), out.size, _ptr(tf32), tf32.shape[1], tf32.shape[0], _ptr(out))
     return out
+
+
+# ------------------------------------------------ histogram and tissue peaks
+
+def histogram256(raw):
+    """256-bin histogram of I_norm (bins decided in float32) -> uint64[256]."""
+    L = _load()
+    r32 = _c(raw, np.float32).ravel()
+    h = np.zeros(256, np.uint64)
+    L.or_histogram256(_ptr(r32), r32.size, float(r32.min()), float(r32.max()), _ptr(h))
+    return h
+
+
+def tissue_peaks(hist, lo=1, hi=254):
+    """(peak bins ascending (3,), count, smoothed histogram) of a 256-bin histogram."""
+    L = _load()
+    h = _c(hist, np.uint64)
+    peaks = np.zeros(3, np.int32)
+    sm = np.zeros(256, np.uint64)
+    cnt = L.or_tissue_peaks(_ptr(h), int(lo), int(hi), _ptr(peaks), _ptr(sm))
+    return peaks, int(cnt), sm
 
 
 # ------------------------------------------------------------- vesselness

@@ -1075,3 +1075,66 @@ void or_render_grad(const double *In, const double *V, const int *n, const doubl
     free(g);
     free(Hs);
 }
+
+/* ------------------------------------------- 256-bin histogram and tissue peaks */
+
+/* 256-bin density of I_norm (Sec. 2.2): bin j = min(floor(I_norm * 256), 255), with
+ * I_norm formed in float32 exactly as for the brick grid (the bin is an integer
+ * decision that must match the kernel's bit for bit). raw: float32 or uint16 values. */
+void or_histogram256(const float *raw, int64_t n, float imin, float imax, uint64_t *hist) {
+    volatile float range = imax - imin;
+    for (int j = 0; j < 256; ++j) hist[j] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        volatile float d = raw[i] - imin;
+        volatile float r = d / range;
+        volatile float x = r * 256.0f;
+        int j = (int)x;
+        if (j > 255) j = 255;
+        if (j < 0) j = 0;
+        hist[j] += 1;
+    }
+}
+
+/* Tri-modal peak extraction (Sec. 2.2, Tables 1-2; the paper names the result,
+ * not the procedure). Reading: smooth the histogram with the binomial kernel
+ * [1 4 6 4 1] (integer weights, clamp-to-edge, no division); a bin j in
+ * [lo, hi] is a peak if s[j] > s[j-1] and s[j] >= s[j+1]; keep the three peaks
+ * with the largest s (ties to the lower bin) and return their bins in ascending
+ * order in peaks[0..2]. Returns the number of peaks found (<= 3); smoothed
+ * (nullable, 256 entries) receives s. Integer arithmetic only. */
+int or_tissue_peaks(const uint64_t *hist, int lo, int hi, int *peaks, uint64_t *smoothed) {
+    static const int w[5] = {1, 4, 6, 4, 1};
+    uint64_t s[256];
+    for (int j = 0; j < 256; ++j) {
+        uint64_t acc = 0;
+        for (int t = -2; t <= 2; ++t) acc += (uint64_t)w[t + 2] * hist[clampi(j + t, 0, 255)];
+        s[j] = acc;
+        if (smoothed) smoothed[j] = acc;
+    }
+    if (lo < 1) lo = 1;
+    if (hi > 254) hi = 254;
+    int best[3] = {-1, -1, -1};
+    for (int j = lo; j <= hi; ++j) {
+        if (!(s[j] > s[j - 1] && s[j] >= s[j + 1])) continue;
+        /* insert into the top three by (s descending, j ascending) */
+        for (int q = 0; q < 3; ++q) {
+            if (best[q] < 0 || s[j] > s[best[q]]) {
+                for (int r = 2; r > q; --r) best[r] = best[r - 1];
+                best[q] = j;
+                break;
+            }
+        }
+    }
+    int cnt = 0;
+    for (int q = 0; q < 3; ++q)
+        if (best[q] >= 0) peaks[cnt++] = best[q];
+    for (int a = 0; a < cnt; ++a) /* ascending bins */
+        for (int b = a + 1; b < cnt; ++b)
+            if (peaks[b] < peaks[a]) {
+                int t = peaks[a];
+                peaks[a] = peaks[b];
+                peaks[b] = t;
+            }
+    for (int q = cnt; q < 3; ++q) peaks[q] = -1;
+    return cnt;
+}
