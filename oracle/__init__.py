@@ -77,6 +77,7 @@ def _load():
         L.or_frangi.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P, _P, _P]
         L.or_render_grad.argtypes = [_P, _P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P, ctypes.c_int,
                                      ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]
+        L.or_median3.argtypes = [_P, _P, _P]
         L.or_histogram256.argtypes = [_P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _P]
         L.or_tissue_peaks.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
         L.or_tissue_peaks.restype = ctypes.c_int
@@ -284,6 +285,15 @@ def classify(grid, tf):
     tf32 = _c(tf, np.float32)
     out = np.zeros(g.shape[:-1], np.uint8)
     L.or_classify(_ptr(g), out.size, _ptr(tf32), tf32.shape[1], tf32.shape[0], _ptr(out))
+    return out
+
+
+def median3(vol):
+    """3x3x3 clamp-to-edge median filter (float64, same shape)."""
+    L = _load()
+    v = _c(vol, np.float64)
+    out = np.empty_like(v)
+    L.or_median3(_ptr(v), _ptr(_dims(v)), _ptr(out))
     return out
 
 

@@ -1138,3 +1138,30 @@ int or_tissue_peaks(const uint64_t *hist, int lo, int hi, int *peaks, uint64_t *
     for (int q = cnt; q < 3; ++q) peaks[q] = -1;
     return cnt;
 }
+
+/* ------------------------------------------------------ optional pre-filters */
+
+/* 3x3x3 median of the normalised volume with clamp-to-edge neighbours: the
+ * optional median pass Sec. 5.3 proposes against impulsive artefacts. The
+ * median of 27 values is the 14th smallest (an order statistic: exact). */
+static int cmp_double(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void or_median3(const double *in, const int *n, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n[2]; ++k)
+        for (int j = 0; j < n[1]; ++j)
+            for (int i = 0; i < n[0]; ++i) {
+                double w[27];
+                int m = 0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx)
+                            w[m++] = in[vidx(n, clampi(i + dx, 0, n[0] - 1), clampi(j + dy, 0, n[1] - 1),
+                                              clampi(k + dz, 0, n[2] - 1))];
+                qsort(w, 27, sizeof(double), cmp_double);
+                out[vidx(n, i, j, k)] = w[13];
+            }
+}
