@@ -26,4 +26,6 @@ def test_median_removes_impulses_and_keeps_constants_and_ramps():
     v[4, 5, 5] = 1.0  # isolated impulse
     np.testing.assert_array_equal(oracle.median3(v), np.full(v.shape, 0.3))
     r = ph.ramp_volume((11, 10, 9), (1, 1, 1), (0.01, 0.02, 0.03))
-    np.testing.assert_allclose(oracle.median3(r), r, atol=1e-15)  # monotone in every axis: median = centre
+    # a linear ramp's 27 neighbours are symmetric about the centre value away from
+    # the clamped border, so the median is the centre there
+    np.testing.assert_allclose(oracle.median3(r)[1:-1, 1:-1, 1:-1], r[1:-1, 1:-1, 1:-1], atol=1e-15)
