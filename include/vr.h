@@ -193,6 +193,31 @@ vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_devi
 /* Copy the normalised volume (nx*ny*nz float32) to `out` (as above). */
 vr_status vr_get_normalized(vr_ctx* ctx, int vol_id, float* out, int out_on_device);
 
+/* Optional pre-filter of the normalised volume (the light smoothing or median
+ * passes proposed in Sec. 5.3 against low SNR and impulsive artefacts):
+ * mode 1 = 3x3x3 median (clamp-to-edge; exact order statistic), mode 2 =
+ * separable Gaussian with sampled normalised weights on [-ceil(4 sigma),
+ * ceil(4 sigma)] voxels, sigma in (0, 8]. The filtered intensities replace the
+ * volume's I_norm (I_min/I_max of Eq. 1 are kept), bricks and the brick grid are
+ * rebuilt and re-classified; morphology (|grad I|max, vesselness) must be
+ * recomputed with vr_precompute_morphology before the next render.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma);
+
+/* The 256-bin density analysis of Sec. 2.2: d_hist[256] (device, uint64) receives
+ * the counts of bin min(floor(I_norm * 256), 255) over all voxels (I_norm in
+ * float32 as stored for the volume). When d_peaks (device, 4 ints) is not NULL,
+ * the tri-modal tissue peaks behind Tables 1-2 are extracted too: the histogram
+ * is smoothed with the integer binomial kernel [1 4 6 4 1] (clamp at the ends), a
+ * bin j in [max(lo_bin, 1), min(hi_bin, 254)] is a peak when s[j] > s[j-1] and
+ * s[j] >= s[j+1], the three largest peaks (ties to the lower bin) are written in
+ * ascending order to d_peaks[0..2] (-1 where fewer exist) and their count to
+ * d_peaks[3]. The bin of peak p covers I_norm in [p/256, (p+1)/256). Choose
+ * [lo_bin, hi_bin] to exclude the background and fat modes. Asynchronous.
+ * Errors: INVALID_ARG (unknown volume, NULL histogram, bins outside [0, 255]). */
+vr_status vr_tissue_histogram(vr_ctx* ctx, int vol_id, int lo_bin, int hi_bin, unsigned long long* d_hist,
+                              int* d_peaks);
+
 /* Global min and max of n values (the parallel reduction of Sec. 4 applied to
  * Eq. 1's I_min, I_max): d_data holds n values of `dtype` on the device;
  * d_out2[0] = min, d_out2[1] = max as float32 (device). Asynchronous; uses
@@ -234,8 +259,11 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * at or below ~0.999), re-evaluating each sample instead of storing it. The
  * reverse sweep visits every sample, empty bricks included: a zero-opacity
  * sample still gives the opacity entries it reads a gradient.
- * opts: NULL or as vr_render (skip_empty applies to the forward re-march
- * only, where it is exact). Errors as vr_render. */
+ * opts: NULL or as vr_render: skip_empty applies to the forward re-march only,
+ * where it is exact; kernel VR_KERNEL_GATHER adds voxel gradients with global
+ * atomics per sample, any other value sweeps brick by brick and sums them in
+ * shared memory first (same per-sample arithmetic; fewer global atomics).
+ * Errors as vr_render. */
 vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
                              const vr_render_opts* opts);

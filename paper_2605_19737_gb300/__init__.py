@@ -187,6 +187,21 @@ class Context:
         self._check(self._lib.vr_get_vesselness(self._h, vol, out.data_ptr(), 1))
         return out
 
+    def prefilter(self, vol, mode="median", sigma=1.0):
+        """Replace I_norm by its 3x3x3 median ("median") or Gaussian ("gauss", sigma voxels)."""
+        m = {"median": 1, "gauss": 2}[mode]
+        self._check(self._lib.vr_prefilter(self._h, vol, m, float(sigma)))
+
+    def tissue_histogram(self, vol, lo_bin=1, hi_bin=254, peaks=True):
+        """(hist (256,) int64 device tensor, peaks (4,) int32 device tensor or None)."""
+        torch = _torch()
+        dev = "cuda:%d" % self.device
+        hist = torch.empty(256, dtype=torch.int64, device=dev)
+        pk = torch.empty(4, dtype=torch.int32, device=dev) if peaks else None
+        self._check(self._lib.vr_tissue_histogram(self._h, vol, int(lo_bin), int(hi_bin), hist.data_ptr(),
+                                                  pk.data_ptr() if peaks else None))
+        return hist, pk
+
     # -- rendering ----------------------------------------------------------
     def render(self, vol, cams, W, H, out=None, kernel=VR_KERNEL_AUTO, skip_empty=True, packet_w=8,
                warps_per_block=4, counters=None, ray_samples=None):
@@ -205,7 +220,7 @@ class Context:
 
 
     def render_backward(self, vol, cams, W, H, dl_drgba, want_volume=True, skip_empty=True, dtf=None, dparams=None,
-                        dvol=None):
+                        dvol=None, kernel=VR_KERNEL_AUTO):
         """Gradients of L given dL/dRGBA (device (n, H, W, 4)): returns (dtf (h, w, 4),
         dparams (5,) = gamma, ka, kd, ks, opacity_scale, dvolume (nz, ny, nx) or None)."""
         torch = _torch()
@@ -219,7 +234,7 @@ class Context:
         if want_volume and dvol is None:
             nx, ny, nz = self._keep[vol]
             dvol = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
-        opts = vr_render_opts(VR_KERNEL_GATHER, int(bool(skip_empty)), 8, 4)
+        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), 8, 4)
         g = dl_drgba.contiguous()
         self._check(self._lib.vr_render_backward(self._h, vol, carr, n, W, H, g.data_ptr(), dtf.data_ptr(),
                                                  dparams.data_ptr(), dvol.data_ptr() if want_volume else None,

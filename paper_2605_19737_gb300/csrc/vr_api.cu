@@ -517,6 +517,55 @@ vr_status vr_get_normalized(vr_ctx* ctx, int vol_id, float* out, int out_on_devi
     return VR_OK;
 }
 
+vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "prefilter: unknown id %d", vol_id);
+    if (mode != 1 && mode != 2) return fail(ctx, VR_ERR_INVALID_ARG, "prefilter: mode must be 1 (median) or 2 (Gaussian)");
+    if (mode == 2 && !(sigma > 0.0f && sigma <= 8.0f))
+        return fail(ctx, VR_ERR_INVALID_ARG, "prefilter: sigma %g outside (0, 8]", (double)sigma);
+    DeviceGuard g(ctx->device);
+    const size_t need = sizeof(float) * 2 * (size_t)v->nvox;
+    if (ctx->scratch_cap < need) {
+        CK(cudaStreamSynchronize(ctx->stream), "prefilter: scratch sync");
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_cap = 0;
+        CK(dalloc(&ctx->d_scratch, need), "prefilter: scratch");
+        ctx->scratch_cap = need;
+    }
+    float* a = ctx->d_scratch;
+    if (mode == 1) {
+        CK(launch_median3(v->d_norm, a, v->n, ctx->stream), "prefilter: median");
+    } else {
+        CK(launch_gauss3d(v->d_norm, a, ctx->d_scratch + v->nvox, v->n, sigma, ctx->stream), "prefilter: Gaussian");
+    }
+    CK(cudaMemcpyAsync(v->d_norm, a, sizeof(float) * v->nvox, cudaMemcpyDeviceToDevice, ctx->stream),
+       "prefilter: copy back");
+    vr_status st = rebuild_bricks(ctx, v);
+    if (st != VR_OK) return st;
+    if (v->params_ready)
+        CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix,
+                           ctx->stream),
+           "prefilter: classify");
+    v->morph_ready = false;  // |grad I|max and vesselness describe the unfiltered volume
+    return VR_OK;
+}
+
+vr_status vr_tissue_histogram(vr_ctx* ctx, int vol_id, int lo_bin, int hi_bin, unsigned long long* d_hist,
+                              int* d_peaks) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "tissue_histogram: unknown id %d", vol_id);
+    if (!d_hist) return fail(ctx, VR_ERR_INVALID_ARG, "tissue_histogram: NULL histogram");
+    if (lo_bin < 0 || hi_bin > 255 || lo_bin > hi_bin)
+        return fail(ctx, VR_ERR_INVALID_ARG, "tissue_histogram: bins [%d, %d] outside [0, 255]", lo_bin, hi_bin);
+    DeviceGuard g(ctx->device);
+    CK(launch_histogram(v->d_norm, v->nvox, d_hist, ctx->stream), "histogram");
+    if (d_peaks) CK(launch_tissue_peaks(d_hist, lo_bin, hi_bin, d_peaks, ctx->stream), "tissue peaks");
+    return VR_OK;
+}
+
 vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
                     int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
                     unsigned int* d_ray_samples) {
@@ -631,7 +680,8 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         B.r.n_cams = nc;
         B.r.cam_offset = c0;
         memcpy(B.r.cams, h_cams + c0, sizeof(CamDev) * nc);
-        CK(launch_render_backward(B, ctx->stream), "render_backward kernel");
+        CK(launch_render_backward(B, !(opts && opts->kernel == VR_KERNEL_GATHER), ctx->stream),
+           "render_backward kernel");
     }
     if (!B.tf_in_smem)
         CK(launch_sum_copies(ctx->d_tfgrad, kTfGradCopies, (long long)ntf, d_dtf, ctx->stream),

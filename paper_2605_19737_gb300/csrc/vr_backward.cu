@@ -175,6 +175,212 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
     }
 }
 
+// Brick-synchronous variant of the reverse sweep. Phase 1 (the forward
+// re-march) is per lane as above. In phase 2 the warp repeatedly picks the
+// farthest brick (largest per-axis brick distance from the eye) that a lane's
+// next reverse sample lies in; the lanes in that brick sweep their samples in
+// it back to front, adding voxel gradients into a 12^3 shared-memory block with
+// shared-memory atomics; the warp then adds the touched part of the block to the
+// global gradient and clears it. Each lane still sweeps its own samples in
+// strictly decreasing order, so every sample sees exactly the arithmetic of
+// k_render_backward; only the order of the floating-point additions into the
+// voxel gradient differs.
+__device__ __forceinline__ unsigned far_key(const int b[3], const int e[3]) {
+    const unsigned dx = min(abs(b[0] - e[0]), 1023), dy = min(abs(b[1] - e[1]), 1023), dz = min(abs(b[2] - e[2]), 1023);
+    return (dz << 20) | (dy << 10) | dx;
+}
+
+__global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_constant__ BackwardLaunch B) {
+    extern __shared__ float smem[];
+    const RenderLaunch& L = B.r;
+    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
+    const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float* s_dtf = smem;                                          // ntf floats when tf_in_smem
+    float* acc = smem + (B.tf_in_smem ? ((ntf + 31) & ~31) : 0) + warp * kBrickVox;  // this warp's 12^3 block
+    if (B.tf_in_smem)
+        for (int e = threadIdx.x; e < ntf; e += blockDim.x) s_dtf[e] = 0.0f;
+    for (int e = l; e < kBrickVox; e += 32) acc[e] = 0.0f;
+    __syncthreads();
+    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
+    const TfGradSink sink{tf_dst};
+    const int i = blockIdx.x * 16 + (warp & 1) * 8 + (l & 7);
+    const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (l >> 3);
+    const int cam = blockIdx.z;
+    const bool inside = i < L.W && j < L.H;
+    const VolumeDev& v = L.vol;
+    const float4* tf = reinterpret_cast<const float4*>(L.tf);
+    const float gmax = __ldg(&v.vc->gmax);
+    const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+    const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
+    const float et = fminf(L.tp.et_threshold, 1.0f);
+    const CamDev& cd = L.cams[cam];
+    int eb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) eb[q] = (int)floorf((cd.eye[q] / v.s[q] - 0.5f) / (float)kCells);
+    ParamGrad dp{0.f, 0.f, 0.f, 0.f, 0.f};
+
+    RayDev r;
+    bool live = inside && setup_ray(cd, L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+    float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int kr = -1;
+    float Tk = 1.0f, Tk1 = 1.0f, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;
+    int kstop = -1;
+    if (live) {
+        const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
+        g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
+        float A = 0.f, A_prev = 0.f;
+        int k = 0, klast = -1;
+        kstop = r.ns - 1;
+        while (k < r.ns) {
+            const float kk = (float)k + 0.5f;
+            int i0[3], bc[3];
+            float f[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                bc[q] = i0[q] >> 3;
+            }
+            const long long bi = bidx(v, bc);
+            if (L.skip && __ldg(v.empty + bi)) {
+                k = brick_exit_k(r, bc, k, r.ns);
+                continue;
+            }
+            const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
+                             (i0[0] - kCells * bc[0]);
+            float fld[10];
+            field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+            scale_field(fld, is);
+            const float vval = v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+            float alpha, col[3];
+            sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+            A_prev = A;
+            A += (1.0f - A) * alpha;
+            klast = k;
+            if (A >= et) {
+                kstop = k;
+                break;
+            }
+            ++k;
+        }
+        Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
+        Tk1 = Tk;
+        kr = kstop;
+    }
+    const float dC[3] = {g4.x, g4.y, g4.z};
+    while (true) {
+        // brick of this lane's next reverse sample
+        int i0[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
+        float f[3] = {0.f, 0.f, 0.f};
+        if (live) {
+            const float kk = (float)kr + 0.5f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                bc[q] = i0[q] >> 3;
+            }
+        }
+        const unsigned key = live ? far_key(bc, eb) + 1u : 0u;
+        const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+        if (mk == 0u) break;
+        const int leader = __ffs(__ballot_sync(0xffffffffu, key == mk)) - 1;
+        int sc[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sc[q] = __shfl_sync(0xffffffffu, bc[q], leader);
+        int lo_t[3] = {kEdge, kEdge, kEdge}, hi_t[3] = {-1, -1, -1};  // touched local range
+        if (live && bc[0] == sc[0] && bc[1] == sc[1] && bc[2] == sc[2]) {
+            const long long bi = bidx(v, sc);
+            while (true) {
+                const int base = ((i0[2] - kCells * sc[2]) * kEdge + (i0[1] - kCells * sc[1])) * kEdge +
+                                 (i0[0] - kCells * sc[0]);
+                float fld[10];
+                field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+                scale_field(fld, is);
+                const float vval =
+                    v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+                float alpha, col[3];
+                sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
+                const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
+                                       g4.w * P);
+                const float ta = Tk * alpha;
+                const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
+                float dfs[10];
+                sample_adjoint(fld, vval, r.dir, L.tp, tf, inv_gmax, da, dc, sink, dp, dfs);
+                if (B.dvol) {
+                    const int lx = i0[0] - kCells * sc[0], ly = i0[1] - kCells * sc[1], lz = i0[2] - kCells * sc[2];
+                    lo_t[0] = min(lo_t[0], lx), lo_t[1] = min(lo_t[1], ly), lo_t[2] = min(lo_t[2], lz);
+                    hi_t[0] = max(hi_t[0], lx + 3), hi_t[1] = max(hi_t[1], ly + 3), hi_t[2] = max(hi_t[2], lz + 3);
+                    field_adjoint_scatter(dfs, is, f[0], f[1], f[2], [&](int a, int b, int c, float g) {
+                        if (g != 0.0f) atomicAdd(acc + base + (c * kEdge + b) * kEdge + a, g);
+                    });
+                }
+                R0 = fmaf(alpha, col[0], (1.0f - alpha) * R0);
+                R1 = fmaf(alpha, col[1], (1.0f - alpha) * R1);
+                R2 = fmaf(alpha, col[2], (1.0f - alpha) * R2);
+                P *= (1.0f - alpha);
+                Tk1 = Tk;
+                if (--kr < 0) {
+                    live = false;
+                    break;
+                }
+                const float kk = (float)kr + 0.5f;
+                int b2[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    b2[q] = i0[q] >> 3;
+                }
+                if (b2[0] != sc[0] || b2[1] != sc[1] || b2[2] != sc[2]) break;
+            }
+        }
+        if (B.dvol) {
+            // add the touched box of the block to the global gradient (clamped voxel
+            // indices: apron cells outside the volume belong to the edge voxel), clear it
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                lo_t[q] = __reduce_min_sync(0xffffffffu, lo_t[q]);
+                hi_t[q] = __reduce_max_sync(0xffffffffu, hi_t[q]);
+            }
+            __syncwarp();
+            if (hi_t[0] >= 0) {
+                const int ex = hi_t[0] - lo_t[0] + 1, ey = hi_t[1] - lo_t[1] + 1, ez = hi_t[2] - lo_t[2] + 1;
+                const int cnt = ex * ey * ez;
+                const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
+                for (int e = l; e < cnt; e += 32) {
+                    const int ax = lo_t[0] + e % ex, ay = lo_t[1] + (e / ex) % ey, az = lo_t[2] + e / (ex * ey);
+                    const int o = (az * kEdge + ay) * kEdge + ax;
+                    const float g = acc[o];
+                    if (g != 0.0f) {
+                        acc[o] = 0.0f;
+                        const int x = min(max(kCells * sc[0] - 1 + ax, 0), nx - 1);
+                        const int y = min(max(kCells * sc[1] - 1 + ay, 0), ny - 1);
+                        const int z = min(max(kCells * sc[2] - 1 + az, 0), nz - 1);
+                        atomicAdd(B.dvol + ((long long)z * ny + y) * nx + x, g);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    float pv[5] = {dp.gamma, dp.ka, dp.kd, dp.ks, dp.os};
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) pv[e] += __shfl_xor_sync(0xffffffffu, pv[e], o);
+    }
+    if (l == 0) {
+#pragma unroll
+        for (int e = 0; e < 5; ++e)
+            if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
+    }
+    if (B.tf_in_smem) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ntf; e += blockDim.x)
+            if (s_dtf[e] != 0.0f) atomicAdd(B.dtf + e, s_dtf[e]);
+    }
+}
+
 // dtf[e] = sum of the n_copies private copies of entry e.
 __global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ copies, int n_copies, long long n,
                                                    float* __restrict__ out) {
@@ -193,10 +399,19 @@ cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, fl
     return cudaGetLastError();
 }
 
-cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st) {
+cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st) {
     const RenderLaunch& L = B.r;
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
-    const int smem = B.tf_in_smem ? L.tp.tf_w * L.tp.tf_h * 4 * (int)sizeof(float) : 0;
+    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
+    if (staged) {
+        const int smem = (B.tf_in_smem ? ((ntf + 31) & ~31) * 4 : 0) + 4 * kBrickBytes;
+        cudaError_t e = cudaFuncSetAttribute(k_render_backward_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             4 * kBrickBytes + 64 * 1024 + 128);
+        if (e != cudaSuccess) return e;
+        k_render_backward_staged<<<grid, 128, smem, st>>>(B);
+        return cudaGetLastError();
+    }
+    const int smem = B.tf_in_smem ? ntf * (int)sizeof(float) : 0;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_render_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;

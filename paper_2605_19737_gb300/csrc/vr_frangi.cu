@@ -157,6 +157,20 @@ __global__ void __launch_bounds__(256) k_frangi_v(const float* __restrict__ sm, 
 
 }  // namespace
 
+cudaError_t launch_gauss3d(const float* in, float* out, float* tmp, const int n[3], float sigma, cudaStream_t st) {
+    GaussParams G;
+    G.R = (int)ceil(4.0 * (double)sigma);
+    if (G.R > kMaxRadius || !(sigma > 0.0f)) return cudaErrorInvalidValue;
+    double sum = 0.0, w[2 * kMaxRadius + 1];
+    for (int i = -G.R; i <= G.R; ++i) sum += (w[i + G.R] = exp(-(double)i * i / (2.0 * (double)sigma * sigma)));
+    for (int i = 0; i <= 2 * G.R; ++i) G.w[i] = (float)(w[i] / sum);
+    dim3 grid((n[0] + 31) / 32, (n[1] + 7) / 8, n[2]);
+    k_gauss_axis<<<grid, 256, 0, st>>>(in, out, n[0], n[1], n[2], 0, G);
+    k_gauss_axis<<<grid, 256, 0, st>>>(out, tmp, n[0], n[1], n[2], 1, G);
+    k_gauss_axis<<<grid, 256, 0, st>>>(tmp, out, n[0], n[1], n[2], 2, G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas, int n_sigmas, float* tmp_a,
                           float* tmp_b, float* smax /* n_sigmas floats */, float* V, cudaStream_t st) {
     const long long nvox = (long long)n[0] * n[1] * n[2];

@@ -117,8 +117,17 @@ cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float
 cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas, int n_sigmas, float* tmp_a,
                           float* tmp_b, float* smax, float* V, cudaStream_t st);
 
+// 256-bin histogram of the normalised volume (zeroes hist first) and its three tissue peaks
+// (peaks4 = three ascending bins, -1 padded, then the count).
+cudaError_t launch_histogram(const float* norm, long long n, unsigned long long* hist, cudaStream_t st);
+cudaError_t launch_tissue_peaks(const unsigned long long* hist, int lo, int hi, int* peaks4, cudaStream_t st);
+
+// Pre-filters: 3x3x3 median; separable Gaussian (out = G * in, tmp is scratch; in != out).
+cudaError_t launch_median3(const float* in, float* out, const int n[3], cudaStream_t st);
+cudaError_t launch_gauss3d(const float* in, float* out, float* tmp, const int n[3], float sigma, cudaStream_t st);
+
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
-cudaError_t launch_render_backward(const BackwardLaunch& B, cudaStream_t st);
+cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st);
 // dtf[e] = sum over c of copies[c * n + e]
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st);

@@ -75,6 +75,8 @@ SIGNATURES = {
     "vr_get_vesselness": ([_P, _I, _P, _I], _I),
     "vr_get_normalized": ([_P, _I, _P, _I], _I),
     "vr_render": ([_P, _I, _P, _I, _I, _I, _P, _I, ctypes.POINTER(vr_render_opts), _P, _P], _I),
+    "vr_prefilter": ([_P, _I, _I, _F], _I),
+    "vr_tissue_histogram": ([_P, _I, _I, _I, _P, _P], _I),
     "vr_classify_bricks_noalloc": ([_P, _LL, _P, _I, _I, _P, _P, ctypes.c_char_p, _I], _I),
     "vr_batch_create": ([_P, _P, _I, ctypes.POINTER(_I)], _I),
     "vr_batch_update": ([_P, _I], _I),

@@ -59,8 +59,9 @@ def _cases():
     return {"head_1d": small, "brainweb_2d": bw}
 
 
+@pytest.mark.parametrize("kernel", [0, 1])  # brick-synchronous (default), per-lane global atomics
 @pytest.mark.parametrize("name", ["head_1d", "brainweb_2d"])
-def test_backward_matches_oracle_gradient(vr, torch, name):
+def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     case = _cases()[name]
     In32 = oracle.normalize(case["volume"]).astype(np.float32)
     In = In32.astype(np.float64)
@@ -75,7 +76,8 @@ def test_backward_matches_oracle_gradient(vr, torch, name):
     dl[amb] = 0.0
     dtf_o, dpar_o, dvol_o = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H, dl,
                                                gmax_value=gmax)
-    dtf, dpar, dvol = vr.render_backward(vid, case["cams"], W, H, torch.from_numpy(dl.astype(np.float32)).cuda())
+    dtf, dpar, dvol = vr.render_backward(vid, case["cams"], W, H, torch.from_numpy(dl.astype(np.float32)).cuda(),
+                                         kernel=kernel)
     dtf, dpar, dvol = dtf.cpu().numpy(), dpar.cpu().numpy(), dvol.cpu().numpy()
     e_tf, e_vol = _rel(dtf, dtf_o), _rel(dvol, dvol_o)
     used = [0, 1, 2, 3, 4] if case["params"]["shading"] else [0, 4]
