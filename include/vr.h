@@ -148,6 +148,20 @@ const char* vr_last_error(vr_ctx* ctx);
 vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype dtype, int nx, int ny, int nz,
                          float sx, float sy, float sz, int* vol_id);
 
+/* Load a single-file NIfTI-1 volume (.nii, either byte order; Sec. 2.1 ingests
+ * NIfTI-1): the first 3D volume of dim[1..3], datatypes uint8, int8, int16,
+ * uint16, int32, uint32, float32, float64; scl_slope/scl_inter applied when
+ * the slope is non-zero; spacing |pixdim[1..3]| converted to mm from the
+ * xyzt_units. uint16 data without scaling is loaded as VR_U16, everything else
+ * as VR_F32, then as vr_load_volume. Errors: INVALID_ARG (unreadable file,
+ * not NIfTI-1, unsupported datatype, dims outside [2, 2048]) and those of
+ * vr_load_volume. */
+vr_status vr_load_nifti(vr_ctx* ctx, const char* path, int* vol_id);
+
+/* Header only, no context or GPU needed: dims (3 ints), spacing in mm
+ * (3 floats) and the NIfTI datatype code; any output may be NULL. */
+vr_status vr_nifti_info(const char* path, int* h_dims, float* h_spacing, int* h_datatype);
+
 /* Free a volume and everything derived from it. */
 vr_status vr_free_volume(vr_ctx* ctx, int vol_id);
 

@@ -128,6 +128,14 @@ class Context:
         self._keep[vid.value] = (nx, ny, nz)
         return vid.value
 
+    def load_nifti(self, path):
+        """Load a .nii file; returns the volume id."""
+        vid = ctypes.c_int()
+        self._check(self._lib.vr_load_nifti(self._h, str(path).encode(), ctypes.byref(vid)))
+        info = nifti_info(path)
+        self._keep[vid.value] = tuple(info["dims"])
+        return vid.value
+
     def dims(self, vol):
         return self._keep[vol]
 
@@ -269,6 +277,18 @@ class Context:
         else:
             self._check(self._lib.vr_batch_render(self._h, batch, ctypes.byref(opts),
                                                   counters.data_ptr() if counters is not None else None))
+
+
+def nifti_info(path):
+    """Header of a .nii file: {"dims": (nx, ny, nz), "spacing": (sx, sy, sz) mm, "datatype": code}."""
+    lib = _vr.load()
+    d = (ctypes.c_int * 3)()
+    s = (ctypes.c_float * 3)()
+    t = ctypes.c_int()
+    st = lib.vr_nifti_info(str(path).encode(), d, s, ctypes.byref(t))
+    if st != 0:
+        raise VRError(st, "not a readable NIfTI-1 file: %s" % path)
+    return {"dims": tuple(d), "spacing": tuple(s), "datatype": t.value}
 
 
 def new_counters(device=0):

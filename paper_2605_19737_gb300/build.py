@@ -19,7 +19,10 @@ OUT = os.path.join(PKG, "libvr.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# Host code is built without floating-point contraction so that host-side arithmetic
+# (NIfTI intensity scaling) rounds the same way on x86-64 and aarch64 hosts.
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+         "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc():

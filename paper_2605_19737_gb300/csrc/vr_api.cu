@@ -177,6 +177,11 @@ vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
 
 }  // namespace
 
+vr_status vr::set_error(vr_ctx* ctx, vr_status status, const char* msg) {
+    if (ctx) ctx->err = msg ? msg : "";
+    return status;
+}
+
 extern "C" {
 
 const char* vr_version(void) { return "vr 1.0 sm_103a"; }

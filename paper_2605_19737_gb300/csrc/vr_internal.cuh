@@ -96,6 +96,9 @@ struct BatchLaunch {
     int skip;
 };
 
+// Record `msg` as the context's last error and return `status`.
+vr_status set_error(vr_ctx* ctx, vr_status status, const char* msg);
+
 // ---------------------------------------------------------------- launchers
 // All return cudaSuccess or the launch error; all enqueue on `st`.
 cudaError_t launch_minmax_partials(const void* data, vr_dtype dt, long long n, float* partials, int nblocks,

@@ -66,6 +66,8 @@ SIGNATURES = {
     "vr_reduce_minmax": ([_P, _P, _I, _LL, _P], _I),
     "vr_load_volume": ([_P, _P, _I, _I, _I, _I, _I, _F, _F, _F, ctypes.POINTER(_I)], _I),
     "vr_free_volume": ([_P, _I], _I),
+    "vr_load_nifti": ([_P, ctypes.c_char_p, ctypes.POINTER(_I)], _I),
+    "vr_nifti_info": ([ctypes.c_char_p, _P, _P, _P], _I),
     "vr_precompute_morphology": ([_P, _I, _P, _I], _I),
     "vr_set_tissue_params": ([_P, _I, ctypes.POINTER(vr_tissue_params)], _I),
     "vr_get_norm": ([_P, _I, _P, _P, _P], _I),
