@@ -167,6 +167,7 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
     L.tf = v->d_tf;
     L.W = W, L.H = H;
     L.skip = skip ? 1 : 0;
+    L.rc = make_ray_consts(W, H, v->s, v->tp.step_vox);
 }
 
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
@@ -728,6 +729,7 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
         d.out = vw.d_out;
         d.W = vw.W;
         d.H = vw.H;
+        d.rc = L.rc;
     }
     CK(cudaMemcpyAsync(b->d_views, b->table.data(), sizeof(ViewDev) * n, cudaMemcpyHostToDevice, ctx->stream),
        "batch: upload views");

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
     ParamGrad dp{0.f, 0.f, 0.f, 0.f, 0.f};
 
     RayDev r;
-    const bool hit = inside && setup_ray(L.cams[cam], L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+    const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     if (hit) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         const float4 g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     ParamGrad dp{0.f, 0.f, 0.f, 0.f, 0.f};
 
     RayDev r;
-    bool live = inside && setup_ray(cd, L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+    bool live = inside && setup_ray(cd, L.rc, i, j, v.n, v.s, r);
     float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
     int kr = -1;
     float Tk = 1.0f, Tk1 = 1.0f, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;

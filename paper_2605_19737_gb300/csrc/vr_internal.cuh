@@ -47,9 +47,28 @@ struct VolumeDev {
     const VolConst* vc;
 };
 
+// Per-launch constants of the ray setup, computed once on the host in FP64.
+struct RayConsts {
+    double two_over_w, two_over_h;  // 2/W, 2/H
+    double inv_s[3];                // 1/spacing
+    double dt, inv_dt;              // sample spacing step_vox * min(s) and its inverse
+};
+
+inline RayConsts make_ray_consts(int W, int H, const float s[3], float step_vox) {
+    RayConsts c;
+    c.two_over_w = 2.0 / (double)W;
+    c.two_over_h = 2.0 / (double)H;
+    for (int q = 0; q < 3; ++q) c.inv_s[q] = 1.0 / (double)s[q];
+    const float smin = s[0] < s[1] ? (s[0] < s[2] ? s[0] : s[2]) : (s[1] < s[2] ? s[1] : s[2]);
+    c.dt = (double)step_vox * (double)smin;
+    c.inv_dt = 1.0 / c.dt;
+    return c;
+}
+
 struct RenderLaunch {
     VolumeDev vol;
     TissueDev tp;
+    RayConsts rc;
     const float* tf;           // [tf_h][tf_w][4]
     float* out;                // [n_cams][H][W][4]
     vr_counters* counters;     // nullable
@@ -80,6 +99,7 @@ constexpr int kTfGradCopies = 64;
 struct ViewDev {
     VolumeDev vol;
     TissueDev tp;
+    RayConsts rc;
     const float* tf;
     CamDev cam;
     float* out;     // [H][W][4]

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
     const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
 
     RayDev r;
-    const bool hit = inside && setup_ray(L.cams[cam], L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+    const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned dense = 0, evald = 0;
     if (hit) march_gather(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald);
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_render_batch(const __grid_constant__ Ba
         const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
         const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
         RayDev r;
-        const bool hit = inside && setup_ray(vw.cam, vw.W, vw.H, i, j, v.n, v.s, vw.tp.step_vox, r);
+        const bool hit = inside && setup_ray(vw.cam, vw.rc, i, j, v.n, v.s, r);
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned dense = 0, evald = 0;
         if (hit)
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
         for (int q = 0; q < 3; ++q) eb[q] = (int)floorf((cd.eye[q] / v.s[q] - 0.5f) / (float)kCells);
 
         RayDev r;
-        bool live = inside && setup_ray(cd, L.W, L.H, i, j, v.n, v.s, L.tp.step_vox, r);
+        bool live = inside && setup_ray(cd, L.rc, i, j, v.n, v.s, r);
         const bool hit = live;
         int k = 0, kstop = -1, cur = -1, bc[3] = {0, 0, 0};
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;

@@ -1,9 +1,9 @@
 // vr_sample.cuh -- per-ray and per-sample device math of the raymarch.
 //
 // Ray setup (pinhole camera, slab intersection, sample count) runs once per
-// ray in FP64 with explicit round-to-nearest operations; it yields the entry
-// point and per-sample step in voxel coordinates as float32 head/tail pairs,
-// from which each sample's cell fraction is formed to ~3e-8 at any depth.
+// ray in FP64; it yields the entry point and per-sample step in voxel
+// coordinates as float32 head/tail pairs, from which each sample's cell
+// fraction is formed to ~3e-8 at any depth.
 //
 // The sample field is the trilinear interpolation of the voxel-wise intensity,
 // central-difference gradient (Eq. 2) and Hessian (Sec. 2.3). Along one axis,
@@ -31,54 +31,58 @@ struct RayDev {
     float dir[3];     // unit ray direction
 };
 
-// Returns false when the ray misses the volume box or has no sample.
-__device__ __forceinline__ bool setup_ray(const CamDev& c, int W, int H, int i, int j, const int n[3],
-                                          const float s[3], float step_vox, RayDev& r) {
-    const double a = __dsub_rn(__ddiv_rn(__dmul_rn(2.0, (double)i + 0.5), (double)W), 1.0);
-    const double b = __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, (double)j + 0.5), (double)H));
+// Ray through pixel (i, j) in FP64: direction normalize(fwd + a right + b up),
+// a = 2(i+1/2)/W - 1, b = 1 - 2(j+1/2)/H; slab intersection with the volume box;
+// t_near = max(t0, 0); ns = #{k : t_near + (k+1/2) dt < t_far}. Divisions are
+// limited to one reciprocal of the length and one per direction component
+// (FP64 division is a long instruction sequence on this part). Returns false
+// when the ray misses the box or has no sample.
+__device__ __forceinline__ bool setup_ray(const CamDev& c, const RayConsts& rc, int i, int j, const int n[3],
+                                          const float s[3], RayDev& r) {
+    const double a = fma((double)i + 0.5, rc.two_over_w, -1.0);
+    const double b = fma(-((double)j + 0.5), rc.two_over_h, 1.0);
     double d[3], o[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         o[q] = (double)c.eye[q];
-        d[q] = __dadd_rn(__dadd_rn((double)c.fwd[q], __dmul_rn(a, (double)c.right[q])),
-                         __dmul_rn(b, (double)c.up[q]));
+        d[q] = fma(b, (double)c.up[q], fma(a, (double)c.right[q], (double)c.fwd[q]));
     }
-    const double len =
-        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2])));
+    const double inv_len = 1.0 / sqrt(fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2])));
 #pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] = __ddiv_rn(d[q], len);
+    for (int q = 0; q < 3; ++q) d[q] *= inv_len;
     double t0 = -INFINITY, t1 = INFINITY;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double hi = __dmul_rn((double)n[q], (double)s[q]);
+        const double hi = (double)n[q] * (double)s[q];
         if (d[q] == 0.0) {
             if (o[q] < 0.0 || o[q] > hi) return false;
             continue;
         }
-        const double ta = __ddiv_rn(__dsub_rn(0.0, o[q]), d[q]);
-        const double tb = __ddiv_rn(__dsub_rn(hi, o[q]), d[q]);
+        const double inv_d = 1.0 / d[q];
+        const double ta = -o[q] * inv_d;
+        const double tb = (hi - o[q]) * inv_d;
         const double lo_t = ta < tb ? ta : tb, hi_t = ta < tb ? tb : ta;
         if (lo_t > t0) t0 = lo_t;
         if (hi_t < t1) t1 = hi_t;
     }
     const double tn = t0 > 0.0 ? t0 : 0.0, tf = t1;
     if (!(tn < tf)) return false;
-    const double dt = __dmul_rn((double)step_vox, (double)fminf(s[0], fminf(s[1], s[2])));
-    // ns = #{k >= 0 : t_near + (k + 1/2) dt < t_far}: estimate, then settle on the exact predicate.
-    long long ns = (long long)ceil(__dsub_rn(__ddiv_rn(__dsub_rn(tf, tn), dt), 0.5));
+    const double dt = rc.dt;
+    // estimate, then settle on the exact predicate t_near + (k + 1/2) dt < t_far
+    long long ns = (long long)ceil(fma(tf - tn, rc.inv_dt, -0.5));
     if (ns < 0) ns = 0;
-    while (ns > 0 && !(__dadd_rn(tn, __dmul_rn((double)(ns - 1) + 0.5, dt)) < tf)) --ns;
-    while (__dadd_rn(tn, __dmul_rn((double)ns + 0.5, dt)) < tf) ++ns;
+    while (ns > 0 && !(fma((double)(ns - 1) + 0.5, dt, tn) < tf)) --ns;
+    while (fma((double)ns + 0.5, dt, tn) < tf) ++ns;
     if (ns == 0) return false;
     r.ns = (int)ns;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double un = __dsub_rn(__ddiv_rn(__dadd_rn(o[q], __dmul_rn(tn, d[q])), (double)s[q]), 0.5);
+        const double un = fma(fma(tn, d[q], o[q]), rc.inv_s[q], -0.5);
         r.uhi[q] = (float)un;
-        r.ulo[q] = (float)__dsub_rn(un, (double)r.uhi[q]);
-        const double st = __ddiv_rn(__dmul_rn(dt, d[q]), (double)s[q]);
+        r.ulo[q] = (float)(un - (double)r.uhi[q]);
+        const double st = dt * d[q] * rc.inv_s[q];
         r.dhi[q] = (float)st;
-        r.dlo[q] = (float)__dsub_rn(st, (double)r.dhi[q]);
+        r.dlo[q] = (float)(st - (double)r.dhi[q]);
         r.dir[q] = (float)d[q];
     }
     return true;
