@@ -41,6 +41,32 @@ FLOPS_PER_SAMPLE = 507
 # by the whole brick store) plus the RGBA float32 image it writes.
 
 
+KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_gb300/csrc/vr_sample.cuh",
+                  "paper_2605_19737_gb300/csrc/vr_internal.cuh")
+
+
+def kernel_source_hash():
+    """sha256 over the sources of the forward raymarch kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of k_render_gather on the benchmark frame, from the ncu
+    capture recorded in profiles/traffic_gather_brainweb_1080p.json -- only while the
+    kernel sources still hash to what was profiled; None otherwise."""
+    p = os.path.join(ROOT, "profiles", "traffic_gather_brainweb_1080p.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    return d.get("dram_bytes_per_launch") if d.get("kernel_source_hash") == kernel_source_hash() else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -319,7 +345,29 @@ def run(args):
                    "grads": "transfer function 256x64x4, 5 uniforms, 181x217x181 voxels",
                    "plain_fwd_gsamples_per_s": value}
 
+    # Per-volume vesselness precompute (sigma 1, 2, 3) on the 256x256x176 vessel phantom.
+    precompute = None
+    if not args.no_batch:
+        from phantoms import workloads as wl
+        vcase = wl.vessel_1080p()
+        vvid = ctx.load_volume(torch.from_numpy(vcase["volume"]).to(dev), vcase["spacing"])
+        pre = []
+        for _ in range(4):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            ctx.precompute_morphology(vvid, vcase["sigmas"])
+            s1.record()
+            torch.cuda.synchronize()
+            pre.append(s0.elapsed_time(s1))
+        ctx.free_volume(vvid)
+        precompute = {"workload": "vessel 256x256x176 float32, Frangi sigma 1, 2, 3 + |grad I|max",
+                      "ms": float(np.median(pre[1:]))}
+
     batched = None if args.no_batch else run_batched(args, ctx, dev, flush)
+    fit = None
+    if not args.no_fit and ws == 1:
+        from paper_2605_19737_gb300 import fit as fitmod
+        fit = fitmod.run(steps=200)
     hbm, smax, peak_kind = _peaks()
     nbricks = int(np.prod([(n - 1 + 7) // 8 for n in vol_np.shape]))
     frame_bytes = nbricks * 6912 + W * H * 16
@@ -343,7 +391,7 @@ def run(args):
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / fp32_peak, "traffic": None,
+                         "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock under load)"
                                         % sm_mhz},
             "hbm_roofline": {"achieved": frame_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -354,6 +402,8 @@ def run(args):
                     "d2h_bytes_per_step": int(W * H * 16), "ms_per_step": 1000.0 * e2e_s},
             "fwd_bwd": fwd_bwd,
             "batched": batched,
+            "precompute": precompute,
+            "fit": fit,
             "gpu_launches": args.steps,  # one raymarch kernel per timed frame
             "clocks": clk,
             "cpu_baseline": cb,
@@ -373,6 +423,7 @@ def main():
     ap.add_argument("--kernel", default="gather", choices=["staged", "gather"])
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fit", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

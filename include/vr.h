@@ -274,9 +274,10 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * reverse sweep visits every sample, empty bricks included: a zero-opacity
  * sample still gives the opacity entries it reads a gradient.
  * opts: NULL or as vr_render: skip_empty applies to the forward re-march only,
- * where it is exact; kernel VR_KERNEL_GATHER adds voxel gradients with global
- * atomics per sample, any other value sweeps brick by brick and sums them in
- * shared memory first (same per-sample arithmetic; fewer global atomics).
+ * where it is exact; kernel VR_KERNEL_STAGED sweeps brick by brick and sums voxel
+ * gradients in shared memory before global atomics, any other value (default)
+ * sweeps each lane independently and adds voxel gradients with global atomics
+ * (same per-sample arithmetic; the default is the faster one measured).
  * Errors as vr_render. */
 vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
