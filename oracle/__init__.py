@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
         ("gamma", ctypes.c_double), ("kappa_ref", ctypes.c_double), ("w_max", ctypes.c_double),
         ("ka", ctypes.c_double), ("kd", ctypes.c_double), ("ks", ctypes.c_double),
         ("opacity_scale", ctypes.c_double), ("et_threshold", ctypes.c_double),
-        ("step_vox", ctypes.c_double),
+        ("step_vox", ctypes.c_double), ("opacity_ref_step", ctypes.c_double),
     ]
 
 
@@ -105,11 +105,11 @@ def f32(x):
 
 
 def make_params(tf_mode=0, tf_shape=(1, 256), grad_mod=1, shading=0, gamma=0.0, kappa_ref=1.0, w_max=4.0,
-                ka=0.3, kd=0.7, ks=0.2, opacity_scale=1.0, et_threshold=0.99, step_vox=0.5):
+                ka=0.3, kd=0.7, ks=0.2, opacity_scale=1.0, et_threshold=0.99, step_vox=0.5, opacity_ref_step=0.0):
     """Oracle parameter block; every float is first rounded to float32 like the kernel's."""
     h, w = tf_shape
     return Params(tf_mode, w, h, grad_mod, shading, f32(gamma), f32(kappa_ref), f32(w_max), f32(ka),
-                  f32(kd), f32(ks), f32(opacity_scale), f32(et_threshold), f32(step_vox))
+                  f32(kd), f32(ks), f32(opacity_scale), f32(et_threshold), f32(step_vox), f32(opacity_ref_step))
 
 
 # ----------------------------------------------------------------- Eq. 1

@@ -26,7 +26,9 @@
  *     two-sided Phong headlight rgb (ka + kd d) + ks d^16, d = |g-hat . dir|;
  *   - samples at t_k = t_near + (k + 1/2) dt for every t_k < t_far, no jitter
  *     (the deterministic, non-progressive rendering of Sec. 1 and Sec. 4);
- *   - early termination after the first sample with A >= et_threshold.
+ *   - early termination after the first sample with A >= et_threshold;
+ *   - optional step-size opacity correction alpha' = 1 - (1 - alpha)^(dt/dt_ref)
+ *     (off unless opacity_ref_step > 0: the paper composites Eqs. 5-6 as printed).
  * Parity pins: closed forms (homogeneous slab, linear ramp, quadratics), a
  * second brute-force field built from hat functions, library eigen-solvers,
  * brute-force convolution, invariants; see tests/test_oracle_*.py. The
@@ -49,6 +51,7 @@ typedef struct {
     double gamma, kappa_ref, w_max;
     double ka, kd, ks;
     double opacity_scale, et_threshold, step_vox;
+    double opacity_ref_step; /* mm; > 0: opacity corrected to this reference step, 0: Eqs. 5-6 as printed */
 } or_params;
 
 typedef struct {
@@ -291,6 +294,10 @@ static void sample_optics(const or_vol *v, const or_params *P, const double *tf,
     double mg = P->grad_mod ? (gn < 1.0 ? gn : 1.0) : 1.0;
     double w = clampd(1.0 + P->gamma * kappa / P->kappa_ref, 0.0, P->w_max);
     *alpha = clampd(P->opacity_scale * rgba[3] * mg * w, 0.0, 1.0);
+    if (P->opacity_ref_step > 0.0) { /* alpha' = 1 - (1 - alpha)^(dt / dt_ref) */
+        double dt = P->step_vox * fmin(v->s[0], fmin(v->s[1], v->s[2]));
+        *alpha = 1.0 - pow(1.0 - *alpha, dt / P->opacity_ref_step);
+    }
     if (P->shading) {
         double d = fabs(ghat[0] * dir[0] + ghat[1] * dir[1] + ghat[2] * dir[2]);
         double d2 = d * d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;
@@ -540,6 +547,7 @@ int or_render_brute(const double *In, const int *n, const double *s, const or_pa
                         cl = (double *)realloc(cl, sizeof(double) * 3 * cap);
                     }
                     al[ns] = clampd(P->opacity_scale * c4[3] * mg * w, 0.0, 1.0);
+                    if (P->opacity_ref_step > 0.0) al[ns] = 1.0 - pow(1.0 - al[ns], dt / P->opacity_ref_step);
                     double dd = fabs(gh[0] * d[0] + gh[1] * d[1] + gh[2] * d[2]);
                     for (int c = 0; c < 3; ++c)
                         cl[3 * ns + c] = P->shading ? c4[c] * (P->ka + P->kd * dd) + P->ks * pow(dd, 16.0) : c4[c];
@@ -808,7 +816,7 @@ typedef struct {
     int tj, tk;       /* transfer-function cell */
     double tt, tq;    /* its fractions */
     int clamp_x, clamp_y; /* 1 when the lookup coordinate lies inside [0, 1] */
-    double mg, w_inner, w, raw, alpha, d, dot, c[3];
+    double mg, w_inner, w, raw, alpha0, alpha, d, dot, c[3];
 } or_srec;
 
 static void sample_record(const or_vol *v, const or_params *P, const double *tf, const double p[3],
@@ -845,7 +853,12 @@ static void sample_record(const or_vol *v, const or_params *P, const double *tf,
     s->w_inner = 1.0 + P->gamma * s->kappa / P->kappa_ref;
     s->w = clampd(s->w_inner, 0.0, P->w_max);
     s->raw = P->opacity_scale * s->rgba[3] * s->mg * s->w;
-    s->alpha = clampd(s->raw, 0.0, 1.0);
+    s->alpha0 = clampd(s->raw, 0.0, 1.0);
+    s->alpha = s->alpha0;
+    if (P->opacity_ref_step > 0.0) {
+        double dt = P->step_vox * fmin(v->s[0], fmin(v->s[1], v->s[2]));
+        s->alpha = 1.0 - pow(1.0 - s->alpha0, dt / P->opacity_ref_step);
+    }
     s->dot = s->ghat[0] * dir[0] + s->ghat[1] * dir[1] + s->ghat[2] * dir[2];
     s->d = fabs(s->dot);
     double d16 = pow(s->d, 16.0);
@@ -877,7 +890,12 @@ static void sample_adjoint(const or_vol *v, const or_params *P, const double *tf
             drgba[q] += dc[q];
         }
     }
-    /* opacity, Eq. 4 */
+    /* opacity correction, then Eq. 4 */
+    if (P->opacity_ref_step > 0.0) {
+        double dt = P->step_vox * fmin(v->s[0], fmin(v->s[1], v->s[2]));
+        double r = dt / P->opacity_ref_step;
+        da = s->alpha0 < 1.0 ? da * r * pow(1.0 - s->alpha0, r - 1.0) : 0.0;
+    }
     double draw = (s->raw >= 0.0 && s->raw <= 1.0) ? da : 0.0;
     dpar[4] += draw * s->rgba[3] * s->mg * s->w;
     drgba[3] += draw * P->opacity_scale * s->mg * s->w;

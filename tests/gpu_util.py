@@ -18,7 +18,7 @@ def oracle_params(p, tf):
     return oracle.make_params(tf_mode=p["tf_mode"], tf_shape=(h, w), grad_mod=p["grad_mod"], shading=p["shading"],
                               gamma=p["gamma"], kappa_ref=p["kappa_ref"], w_max=p["w_max"], ka=p["ka"], kd=p["kd"],
                               ks=p["ks"], opacity_scale=p["opacity_scale"], et_threshold=p["et_threshold"],
-                              step_vox=p["step_vox"])
+                              step_vox=p["step_vox"], opacity_ref_step=p.get("opacity_ref_step", 0.0))
 
 
 def oracle_render_case(case, V=None, pix_stride=1, params=None, tf=None, brick_empty=None, In=None, v_amb=None):

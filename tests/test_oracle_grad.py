@@ -31,7 +31,8 @@ def _case(mode, seed=61, shading=1, et=2.0):
 
 def _P(p):
     return oracle.Params(p["tf_mode"], p["tf_w"], p["tf_h"], p["grad_mod"], p["shading"], p["gamma"], p["kappa_ref"],
-                         p["w_max"], p["ka"], p["kd"], p["ks"], p["opacity_scale"], p["et_threshold"], p["step_vox"])
+                         p["w_max"], p["ka"], p["kd"], p["ks"], p["opacity_scale"], p["et_threshold"], p["step_vox"],
+                         p.get("opacity_ref_step", 0.0))
 
 
 def _loss(In, sp, cams, tf, pars, dl, gmax):
@@ -39,9 +40,11 @@ def _loss(In, sp, cams, tf, pars, dl, gmax):
     return float(np.sum(dl * r.rgba))
 
 
-@pytest.mark.parametrize("mode,shading,et", [(0, 1, 2.0), (1, 1, 2.0), (0, 0, 2.0), (0, 1, 0.9)])
-def test_oracle_gradient_matches_finite_differences(mode, shading, et):
+@pytest.mark.parametrize("mode,shading,et,ref", [(0, 1, 2.0, 0.0), (1, 1, 2.0, 0.0), (0, 0, 2.0, 0.0), (0, 1, 0.9, 0.0),
+                                                (0, 1, 2.0, 0.8)])
+def test_oracle_gradient_matches_finite_differences(mode, shading, et, ref):
     In, sp, cams, tf, pars, dl = _case(mode, shading=shading, et=et)
+    pars["opacity_ref_step"] = ref
     gmax = oracle.gmax(In, sp)
     dtf, dpar, dIn = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, dl, gmax_value=gmax)
     assert np.abs(dtf).max() > 0 and np.abs(dIn).max() > 0

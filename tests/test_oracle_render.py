@@ -200,3 +200,19 @@ def test_classification_integer_rule():
                     np.uint16).reshape(1, 1, 4, 2)
     e = oracle.classify(grid, tf)[0, 0]
     assert list(e) == [1, 0, 1, 0]
+
+
+@pytest.mark.parametrize("step", [0.5, 0.25, 0.125])
+def test_opacity_correction_makes_slab_step_independent(step):
+    """With alpha' = 1 - (1 - alpha)^(dt/dt_ref), a homogeneous slab of length L
+    accumulates A = 1 - (1 - alpha)^(L/dt_ref) whatever the sample spacing dt."""
+    n = 32
+    In = np.full((n, 8, 8), 0.5)
+    a0 = 0.05
+    tf = ph.tf_constant((0.2, 0.4, 0.6), a0)
+    cam = _axis_cam_z((4.0, 4.0), -10.0)
+    P = oracle.make_params(grad_mod=0, et_threshold=2.0, step_vox=step, opacity_ref_step=1.0)
+    r = oracle.render(In, (1, 1, 1), P, tf, cam[None], 1, 1, gmax_value=1.0)
+    a32 = float(np.float32(a0))
+    assert r.dense[0, 0, 0] == int(n / step)
+    assert r.rgba[0, 0, 0, 3] == pytest.approx(1.0 - (1.0 - a32) ** (n / 1.0), rel=1e-12)
