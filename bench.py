@@ -33,14 +33,16 @@ METRIC = "Gsamples/s & FPS at 1080p (fwd, fwd+bwd) vs plain fwd, % of HBM roofli
 UNIT = "Gsamples/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 operations of one evaluated sample of the raymarch, counted from the
-# algorithm: 56-voxel separable contraction to I, grad, Hessian (368 incl. the
-# 4-tap weights), spacing scale (15), curvature/normalisation (38), transfer
-# function (2D bilinear, 36), Eq. 4 (8), Phong (16), Eqs. 5-6 (8), position (18).
-FLOPS_PER_SAMPLE = 507
-# Unique bytes a frame must move at least: the bricked voxels it touches (bounded
-# by the whole brick store) plus the RGBA float32 image it writes.
-
-
+# algorithm. Shared by all kernels: curvature/normalisation (38), transfer
+# function (2D bilinear, 36), Eq. 4 (8), Phong (16), Eqs. 5-6 (8), position (18)
+# = 124. Field at the sample: from the derived bricks (voxel-wise I, gradient,
+# Hessian), trilinear weights (19) + 8 corners x 10 channels FMA (160) = 179; by
+# the per-sample stencils, the 56-voxel separable contraction (368 incl. the
+# 4-tap weights) + spacing scale (15) = 383.
+FLOPS_PER_SAMPLE = {"gather": 124 + 179, "stencil": 124 + 383, "staged": 124 + 383}
+# Bytes of one brick: derived (9^3 corners x 12 float32) or intensity (12^3 float32).
+BRICK_BYTES = {"gather": 9 * 9 * 9 * 12 * 4, "stencil": 12 ** 3 * 4, "staged": 12 ** 3 * 4}
+DERIVED_BUDGET_BYTES = 16 << 30
 KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_gb300/csrc/vr_sample.cuh",
                   "paper_2605_19737_gb300/csrc/vr_internal.cuh")
 
@@ -265,7 +267,8 @@ def run(args):
     rays, dense, evald = [int(x) for x in ctr.cpu().numpy()[:3]]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    kernel = pkg.VR_KERNEL_STAGED if args.kernel == "staged" else pkg.VR_KERNEL_GATHER
+    kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
+              "stencil": pkg.VR_KERNEL_GATHER_STENCIL}[args.kernel]
 
     def frame():
         ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel)
@@ -370,10 +373,15 @@ def run(args):
         fit = fitmod.run(steps=200)
     hbm, smax, peak_kind = _peaks()
     nbricks = int(np.prod([(n - 1 + 7) // 8 for n in vol_np.shape]))
-    frame_bytes = nbricks * 6912 + W * H * 16
+    kind = args.kernel
+    if kind == "gather" and nbricks * BRICK_BYTES["gather"] > DERIVED_BUDGET_BYTES:
+        kind = "stencil"  # derived bricks are not built above the memory budget
+    # unique bytes a frame must move at least: the bricks it reads (bounded by the
+    # whole brick store) plus the RGBA float32 image it writes
+    frame_bytes = nbricks * BRICK_BYTES[kind] + W * H * 16
     sm_mhz = clk.get("sm_mhz") or smax
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved_tflops = evald * FLOPS_PER_SAMPLE / (ms * 1e-3) / 1e12
+    achieved_tflops = evald * FLOPS_PER_SAMPLE[kind] / (ms * 1e-3) / 1e12
     if rank == 0:
         cb = None
         if ws == 1 and not args.no_cpu_baseline:
@@ -391,6 +399,7 @@ def run(args):
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "flops_per_evaluated_sample": FLOPS_PER_SAMPLE[kind],
                          "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock under load)"
                                         % sm_mhz},
@@ -420,7 +429,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default="gather", choices=["staged", "gather"])
+    ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fit", action="store_true")

@@ -88,6 +88,9 @@ typedef struct {
     float gamma, kappa_ref, w_max;
     float ka, kd, ks;
     float opacity_scale, et_threshold, step_vox;
+    float opacity_ref_step; /* mm; > 0: alpha' = 1 - (1 - alpha)^(dt / opacity_ref_step)
+                               makes the image independent of the sample spacing dt;
+                               0 (default): Eqs. 5-6 as printed */
 } vr_tissue_params;
 
 /* Device-side counters a render may add into (zero them yourself first). */
@@ -100,8 +103,12 @@ typedef struct {
 
 typedef enum {
     VR_KERNEL_AUTO = 0,    /* the fastest measured on GB300 (gather) */
-    VR_KERNEL_GATHER = 1,  /* per-lane gathers from the bricked volume in HBM/L2 */
-    VR_KERNEL_STAGED = 2   /* warp-cooperative brick staging in shared memory */
+    VR_KERNEL_GATHER = 1,  /* per-lane reads of the bricked volume through L1: the voxel-wise
+                              derivatives precomputed by vr_precompute_morphology (8 corners per
+                              sample) when they fit the memory budget, else as GATHER_STENCIL */
+    VR_KERNEL_STAGED = 2,  /* warp-cooperative brick staging in shared memory, per-sample stencils */
+    VR_KERNEL_GATHER_STENCIL = 3  /* per-lane reads, per-sample stencils over the 56 weighted voxels
+                                     of the cell's 4x4x4 neighbourhood (no derived data) */
 } vr_kernel;
 
 typedef struct {
@@ -189,8 +196,8 @@ vr_status vr_get_norm(vr_ctx* ctx, int vol_id, float* imin, float* imax, float* 
 vr_status vr_set_gmax(vr_ctx* ctx, int vol_id, float gmax);
 
 /* Overwrite the normalised intensities of a loaded volume with
- * d_norm[nx*ny*nz] (device, float32, x fastest) and rebuild its bricks and
- * min/max grid; I_min/I_max and |grad I|_max are kept. Used to render or
+ * d_norm[nx*ny*nz] (device, float32, x fastest) and rebuild its bricks, derived
+ * bricks (when built) and min/max grid; I_min/I_max and |grad I|_max are kept. Used to render or
  * differentiate a volume given directly in I_norm units. */
 vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm);
 
@@ -275,10 +282,13 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * sample still gives the opacity entries it reads a gradient.
  * opts: NULL or as vr_render: skip_empty applies to the forward re-march only,
  * where it is exact; kernel VR_KERNEL_STAGED sweeps brick by brick and sums voxel
- * gradients in shared memory before global atomics, any other value (default)
- * sweeps each lane independently and adds voxel gradients with global atomics
- * (same per-sample arithmetic; the default is the faster one measured).
- * Errors as vr_render. */
+ * gradients in shared memory before global atomics (per-sample stencils), any
+ * other value (default) sweeps each lane independently and adds voxel gradients
+ * with global atomics, evaluating samples from the derived bricks when they exist
+ * except under VR_KERNEL_GATHER_STENCIL (same sample field up to rounding; the
+ * default is the faster one measured). The voxel gradient is always the exact
+ * transpose of the per-sample stencils. Errors as vr_render; a kernel value
+ * outside 0..3 is VR_ERR_INVALID_ARG. */
 vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
                              const vr_render_opts* opts);

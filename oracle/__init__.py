@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-FLAG_COUNT, FLAG_ET, FLAG_BRICK, FLAG_VAMB = 1, 2, 4, 8
+FLAG_COUNT, FLAG_ET, FLAG_BRICK, FLAG_VAMB, FLAG_KINK = 1, 2, 4, 8, 16
 
 
 def build(force=False):

@@ -71,6 +71,7 @@ typedef struct {
 #define OR_FLAG_ET 2u
 #define OR_FLAG_BRICK 4u
 #define OR_FLAG_VAMB 8u /* a sample interpolated V from a tie voxel (vesselness transfer function) */
+#define OR_FLAG_KINK 16u /* a sample within rounding of a non-differentiable point (gradients only) */
 
 static inline int64_t vidx(const int *n, int i, int j, int k) {
     return ((int64_t)k * n[1] + j) * n[0] + i;
@@ -270,9 +271,18 @@ void or_tf_sample(const double *tf, int w, int h, double x, double y, double *rg
 
 /* --------------------------------------------------- per-sample optics */
 
-/* Opacity (Eq. 4) and colour of one sample at world point p seen along unit dir. */
-static void sample_optics(const or_vol *v, const or_params *P, const double *tf, const double p[3],
-                          const double dir[3], double *alpha, double col[3]) {
+/* Distance of x to the nearest integer. */
+static double frac_dist(double x) { return fabs(x - floor(x + 0.5)); }
+
+/* Opacity (Eq. 4) and colour of one sample at world point p seen along unit dir.
+ * kink (may be NULL) is set to 1 when the sample sits within float32 rounding of a
+ * point where the opacity or colour is not differentiable in the voxels: a
+ * transfer-function knot or end (lookup coordinate within 2e-4 entries), the clamps
+ * of w(kappa) or of |grad I|/gmax or of alpha at 1 (within 1e-4), or a vanishing
+ * gradient (|grad I| < 1e-4 gmax) where kappa and the shading normal are undefined.
+ * There a float32 evaluation may take the other one-sided derivative. */
+static void sample_optics_k(const or_vol *v, const or_params *P, const double *tf, const double p[3],
+                            const double dir[3], double *alpha, double col[3], int *kink) {
     double fld[11];
     field_at(v, p, fld);
     const double *g = fld + 1, *H = fld + 4;
@@ -292,8 +302,20 @@ static void sample_optics(const or_vol *v, const or_params *P, const double *tf,
     double rgba[4];
     tf_sample(tf, P->tf_w, P->tf_h, fld[0], y, rgba);
     double mg = P->grad_mod ? (gn < 1.0 ? gn : 1.0) : 1.0;
-    double w = clampd(1.0 + P->gamma * kappa / P->kappa_ref, 0.0, P->w_max);
-    *alpha = clampd(P->opacity_scale * rgba[3] * mg * w, 0.0, 1.0);
+    double winner = 1.0 + P->gamma * kappa / P->kappa_ref;
+    double w = clampd(winner, 0.0, P->w_max);
+    double raw = P->opacity_scale * rgba[3] * mg * w;
+    *alpha = clampd(raw, 0.0, 1.0);
+    if (kink) { /* exact zeros and ends are exact in float32 too: no flag there */
+        int k = 0;
+        if (fld[0] != 0.0 && fld[0] != 1.0) k |= frac_dist(clampd(fld[0], 0.0, 1.0) * (P->tf_w - 1)) < 2e-4;
+        if (P->tf_h > 1 && y != 0.0 && y != 1.0) k |= frac_dist(clampd(y, 0.0, 1.0) * (P->tf_h - 1)) < 2e-4;
+        if (P->gamma != 0.0 && gg > 0.0) k |= fabs(winner) < 1e-4 || fabs(winner - P->w_max) < 1e-4;
+        if (P->grad_mod) k |= fabs(gn - 1.0) < 1e-4;
+        k |= fabs(raw - 1.0) < 1e-4;
+        if (P->shading || P->gamma != 0.0 || P->grad_mod || P->tf_mode == 1) k |= gn > 0.0 && gn < 1e-4;
+        *kink = k;
+    }
     if (P->opacity_ref_step > 0.0) { /* alpha' = 1 - (1 - alpha)^(dt / dt_ref) */
         double dt = P->step_vox * fmin(v->s[0], fmin(v->s[1], v->s[2]));
         *alpha = 1.0 - pow(1.0 - *alpha, dt / P->opacity_ref_step);
@@ -305,6 +327,11 @@ static void sample_optics(const or_vol *v, const or_params *P, const double *tf,
     } else {
         for (int c = 0; c < 3; ++c) col[c] = rgba[c];
     }
+}
+
+static void sample_optics(const or_vol *v, const or_params *P, const double *tf, const double p[3],
+                          const double dir[3], double *alpha, double col[3]) {
+    sample_optics_k(v, P, tf, p, dir, alpha, col, NULL);
 }
 
 /* ------------------------------------------------------------ ray setup */
@@ -385,7 +412,9 @@ static void march(const or_vol *v, const or_params *P, const double *tf, const d
             ++ne;
         }
         double alpha, c[3];
-        sample_optics(v, P, tf, p, d, &alpha, c);
+        int kink = 0;
+        sample_optics_k(v, P, tf, p, d, &alpha, c, flags ? &kink : NULL);
+        if (kink) *flags |= OR_FLAG_KINK;
         if (flags && v->v_amb && P->tf_mode == 2) {
             int i0[3];
             double f[3];

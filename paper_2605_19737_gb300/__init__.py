@@ -13,7 +13,7 @@ import numpy as np
 from . import vr as _vr
 from .vr import (  # noqa: F401
     VR_F32, VR_U16, VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL,
-    VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED,
+    VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL,
     vr_camera, vr_tissue_params, vr_counters, vr_render_opts, vr_view,
 )
 
@@ -148,7 +148,8 @@ class Context:
         self._check(self._lib.vr_precompute_morphology(self._h, vol, s.ctypes.data if s.size else None, s.size))
 
     def set_tissue_params(self, vol, tf, tf_mode=0, grad_mod=1, shading=0, gamma=0.0, kappa_ref=1.0, w_max=4.0,
-                          ka=0.3, kd=0.7, ks=0.2, opacity_scale=1.0, et_threshold=0.99, step_vox=0.5):
+                          ka=0.3, kd=0.7, ks=0.2, opacity_scale=1.0, et_threshold=0.99, step_vox=0.5,
+                          opacity_ref_step=0.0):
         """tf: (h, w, 4) float32 RGBA table, numpy (host) or torch (host or device)."""
         if isinstance(tf, np.ndarray):
             tf = np.ascontiguousarray(tf, np.float32)
@@ -157,7 +158,7 @@ class Context:
         h, w = int(tf.shape[0]), int(tf.shape[1])
         p, dev = _ptr(tf)
         tp = vr_tissue_params(int(tf_mode), w, h, p, int(dev), int(grad_mod), int(shading), gamma, kappa_ref,
-                              w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox)
+                              w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox, opacity_ref_step)
         self._check(self._lib.vr_set_tissue_params(self._h, vol, ctypes.byref(tp)))
         self._tf_shape[vol] = (h, w)
 

@@ -97,7 +97,11 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
         dr[1] = dc[1];
         dr[2] = dc[2];
     }
-    // opacity, Eq. 4
+    // step-size opacity correction alpha' = 1 - (1 - alpha)^e, then Eq. 4
+    if (tp.alpha_exp > 0.0f) {
+        const float a0 = fminf(fmaxf(raw, 0.0f), 1.0f);
+        da = a0 < 1.0f ? da * tp.alpha_exp * expf((tp.alpha_exp - 1.0f) * log1pf(-a0)) : 0.0f;
+    }
     const float draw = (raw >= 0.0f && raw <= 1.0f) ? da : 0.0f;
     dp.os += draw * c.w * mg * wk;
     dr[3] = draw * tp.opacity_scale * mg * wk;

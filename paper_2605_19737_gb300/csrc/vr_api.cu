@@ -32,6 +32,7 @@ struct Volume {
     float* d_minmax = nullptr;
     float* d_vessel = nullptr;
     float* d_vbricks = nullptr;
+    float* d_dbricks = nullptr;  // derived bricks (voxel-wise I, gradient, Hessian) or nullptr
     float* d_smax = nullptr;  // per-scale max Hessian norm (8 floats)
     float* d_tf = nullptr;
     size_t tf_cap = 0;
@@ -116,6 +117,7 @@ void free_volume(Volume* v) {
     cudaFree(v->d_minmax);
     cudaFree(v->d_vessel);
     cudaFree(v->d_vbricks);
+    cudaFree(v->d_dbricks);
     cudaFree(v->d_smax);
     cudaFree(v->d_tf);
     cudaFree(v->d_prefix);
@@ -161,6 +163,7 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
     }
     L.vol.bricks = v->d_bricks;
     L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
+    L.vol.dbricks = v->d_dbricks;
     L.vol.empty = v->d_empty;
     L.vol.vc = v->d_vc;
     L.tp = v->tp;
@@ -173,6 +176,7 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
     CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
     CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
+    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
     return VR_OK;
 }
 
@@ -363,6 +367,16 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
             return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: sigma %g outside (0, 8]", (double)h_sigmas[i]);
     DeviceGuard g(ctx->device);
     CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
+    // voxel-wise derivatives for the raymarch (Sec. 2.3), within a memory budget
+    const size_t dbytes = sizeof(float) * (size_t)kDerBrickFloats * v->nbricks;
+    if (!v->d_dbricks && dbytes <= kDerivedBudgetBytes) {
+        cudaError_t e = dalloc(&v->d_dbricks, dbytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            v->d_dbricks = nullptr;  // fall back to the per-sample stencils
+        }
+    }
+    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
     if (n_sigmas > 0) {
         if (!v->d_vessel) {
             CK(dalloc(&v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
@@ -402,6 +416,8 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
         !(tp->opacity_scale >= 0.0f) || !isfinite(tp->opacity_scale) || !isfinite(tp->et_threshold) ||
         !isfinite(tp->ka) || !isfinite(tp->kd) || !isfinite(tp->ks))
         return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: bad scalar parameter");
+    if (!(tp->opacity_ref_step >= 0.0f) || !isfinite(tp->opacity_ref_step))
+        return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: opacity_ref_step must be finite and >= 0");
     if (!(tp->step_vox >= 0.01f && tp->step_vox <= 16.0f))
         return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: step_vox %g outside [0.01, 16]", (double)tp->step_vox);
     if ((tp->grad_mod != 0 && tp->grad_mod != 1) || (tp->shading != 0 && tp->shading != 1))
@@ -433,6 +449,11 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
     d.gamma = tp->gamma, d.kappa_ref = tp->kappa_ref, d.w_max = tp->w_max;
     d.ka = tp->ka, d.kd = tp->kd, d.ks = tp->ks;
     d.opacity_scale = tp->opacity_scale, d.et_threshold = tp->et_threshold, d.step_vox = tp->step_vox;
+    {
+        const double smin = fmin((double)v->s[0], fmin((double)v->s[1], (double)v->s[2]));
+        d.alpha_exp = tp->opacity_ref_step > 0.0f ? (float)((double)tp->step_vox * smin / (double)tp->opacity_ref_step)
+                                                  : 0.0f;
+    }
     CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, tp->tf_w, tp->tf_h, v->d_empty, v->d_prefix, ctx->stream),
        "classify");
     v->params_ready = true;
@@ -585,7 +606,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_set_tissue_params first");
     vr_render_opts o{VR_KERNEL_AUTO, 1, 8, 4};
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 2) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
+    if (o.kernel < 0 || o.kernel > 3) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
     // VR_KERNEL_AUTO picks the per-lane gather kernel: on GB300 the bricked volume stays
     // L1/L2-resident and per-lane marching keeps 91% of lanes busy, while staging one
     // brick per warp idles the lanes outside it (ncu: 58% SIMT efficiency).
@@ -606,6 +627,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.out = dst;
     L.counters = d_counters;
     L.ray_samples = d_ray_samples;
+    if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr;
     L.packet_w = o.packet_w;
     L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
     L.work_counter = ctx->d_work;
@@ -655,6 +677,8 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render_backward: call vr_set_tissue_params first");
     DeviceGuard g(ctx->device);
     const int skip = opts ? opts->skip_empty : 1;
+    if (opts && (opts->kernel < 0 || opts->kernel > 3))
+        return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: bad kernel choice");
     const size_t ntf = (size_t)v->tp.tf_w * v->tp.tf_h * 4;
     CK(cudaMemsetAsync(d_dtf, 0, sizeof(float) * ntf, ctx->stream), "render_backward: zero dtf");
     CK(cudaMemsetAsync(d_dparams, 0, sizeof(float) * 5, ctx->stream), "render_backward: zero dparams");
@@ -662,6 +686,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     BackwardLaunch B;
     memset(&B, 0, sizeof B);
     fill_launch(B.r, v, W, H, skip);
+    if (opts && opts->kernel == VR_KERNEL_GATHER_STENCIL) B.r.vol.dbricks = nullptr;
     B.dl_drgba = d_dl_drgba;
     B.dtf = d_dtf;
     B.dparams = d_dparams;

@@ -36,6 +36,23 @@ __device__ __forceinline__ long long bidx(const VolumeDev& v, const int b[3]) {
     return ((long long)b[2] * v.nb[1] + b[1]) * v.nb[0] + b[0];
 }
 
+// The sample field, from the derived bricks (voxel-wise derivatives) or by the
+// per-sample stencils -- the same linear map of the voxels, either way.
+template <bool kDerived>
+__device__ __forceinline__ void eval_field(const VolumeDev& v, long long bi, const int i0[3], const int bc[3], int base,
+                                           const float f[3], const float is[3], float fld[10]) {
+    if (kDerived) {
+        const int cell =
+            ((i0[2] - kCells * bc[2]) * kDerEdge + (i0[1] - kCells * bc[1])) * kDerEdge + (i0[0] - kCells * bc[0]);
+        field_eval_derived(reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats), cell, f[0], f[1], f[2],
+                           fld);
+    } else {
+        field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+        scale_field(fld, is);
+    }
+}
+
+template <bool kDerived>
 __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     extern __shared__ float s_dtf[];
     const RenderLaunch& L = B.r;
@@ -89,8 +106,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
             const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                              (i0[0] - kCells * bc[0]);
             float fld[10];
-            field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
-            scale_field(fld, is);
+            eval_field<kDerived>(v, bi, i0, bc, base, f, is, fld);
             const float vval = v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
             float alpha, col[3];
             sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
@@ -124,8 +140,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
                 float fld[10];
-                field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
-                scale_field(fld, is);
+                eval_field<kDerived>(v, bi, i0, bc, base, f, is, fld);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 float alpha, col[3];
@@ -412,11 +427,19 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
         return cudaGetLastError();
     }
     const int smem = B.tf_in_smem ? ntf * (int)sizeof(float) : 0;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_render_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (smem > 48 * 1024 && !L.vol.dbricks) {
+        cudaError_t e = cudaFuncSetAttribute(k_render_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
     }
-    k_render_backward<<<grid, 128, smem, st>>>(B);
+    if (L.vol.dbricks) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_render_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_render_backward<true><<<grid, 128, smem, st>>>(B);
+    } else {
+        k_render_backward<false><<<grid, 128, smem, st>>>(B);
+    }
     return cudaGetLastError();
 }
 

@@ -22,6 +22,14 @@ constexpr int kBrickVox = kEdge * kEdge * kEdge;   // 1728 floats
 constexpr int kBrickBytes = kBrickVox * 4;         // 6912 bytes
 constexpr int kMaxCamsPerLaunch = 64;
 
+// Derived bricks: per brick the 9^3 corner voxels [8b, 8b+8] (clamped) of its cells,
+// each as 12 floats = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (mm units), 0, 0:
+// the voxel-wise derivatives of Sec. 2.3, three 16-byte loads per corner.
+constexpr int kDerEdge = 9;
+constexpr int kDerFloats = 12;
+constexpr int kDerBrickFloats = kDerEdge * kDerEdge * kDerEdge * kDerFloats;  // 8748 floats = 34,992 B
+constexpr size_t kDerivedBudgetBytes = (size_t)16 << 30;  // built only below this size
+
 struct CamDev {
     float eye[3], fwd[3], right[3], up[3];
 };
@@ -29,6 +37,7 @@ struct CamDev {
 struct TissueDev {
     int tf_mode, tf_w, tf_h, grad_mod, shading;
     float gamma, kappa_ref, w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox;
+    float alpha_exp;  // dt / opacity_ref_step for the step-size opacity correction; 0 = off
 };
 
 // Per-volume constants that kernels read from device memory (so that host code
@@ -43,6 +52,7 @@ struct VolumeDev {
     float s[3];     // spacing (mm)
     const float* bricks;     // nbricks * kBrickVox
     const float* vbricks;    // vesselness bricks (same layout) or nullptr
+    const float* dbricks;    // derived bricks or nullptr (then the per-sample stencils are used)
     const uint8_t* empty;    // nbricks flags, 1 = skip
     const VolConst* vc;
 };
@@ -130,6 +140,8 @@ cudaError_t launch_normalize(const void* raw, vr_dtype dt, long long n, const fl
                              float* norm, cudaStream_t st);
 cudaError_t launch_make_bricks(const float* norm, const int n[3], const int nb[3], float* bricks, cudaStream_t st);
 cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* grid,
+                                cudaStream_t st);
+cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], const float s[3], float* dbricks,
                                 cudaStream_t st);
 cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], VolConst* vc, cudaStream_t st);
 cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,

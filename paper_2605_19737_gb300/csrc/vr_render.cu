@@ -2,8 +2,10 @@
 //
 // k_render_gather: one thread per ray, a warp covers an 8x4 pixel packet and a
 // CTA a 16x8 tile. Each lane walks its own samples front to back; per sample it
-// gathers the 56 weighted voxels of its cell's 4x4x4 neighbourhood straight
-// from the bricked volume (L1/L2-resident), evaluates the field, Eq. 4 and the
+// reads its cell straight from HBM/L2 through L1 -- the 8 corners of the derived
+// bricks (voxel-wise I, gradient, Hessian: three 16-byte loads per corner) when
+// they were built, else the 56 weighted voxels of the 4x4x4 neighbourhood of the
+// intensity bricks with the separable stencils -- evaluates Eq. 4 and the
 // shading, and composites by Eqs. 5-6. Samples in bricks classified empty are
 // skipped a brick at a time (bit-neutral: their opacity is exactly zero).
 #include "vr_async.cuh"
@@ -38,6 +40,7 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
 
 // Front-to-back march of one ray (Eqs. 4-6) over the bricked volume in HBM/L2,
 // skipping bricks classified empty. Shared by the single-view and batched kernels.
+template <bool kDerived>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
                                              float4& out, unsigned& dense, unsigned& evald) {
@@ -71,8 +74,15 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge + (i0[0] - kCells * bc[0]);
         const long long boff = bi * kBrickVox;
         float fld[10];
-        field_eval(GlobalLoad{v.bricks + boff}, base, f[0], f[1], f[2], fld);
-        scale_field(fld, is);
+        if (kDerived) {
+            const int cell =
+                ((i0[2] - kCells * bc[2]) * kDerEdge + (i0[1] - kCells * bc[1])) * kDerEdge + (i0[0] - kCells * bc[0]);
+            field_eval_derived(reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats), cell, f[0], f[1],
+                               f[2], fld);
+        } else {
+            field_eval(GlobalLoad{v.bricks + boff}, base, f[0], f[1], f[2], fld);
+            scale_field(fld, is);
+        }
         const float vval = v.vbricks ? value_eval(GlobalLoad{v.vbricks + boff}, base, f[0], f[1], f[2]) : 0.0f;
         float alpha, col[3];
         sample_optics(fld, vval, r.dir, tp, tf, inv_gmax, alpha, col);
@@ -93,7 +103,9 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     evald = ne;
 }
 
-__global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ RenderLaunch L) {
+// 7 resident CTAs per SM for the derived-brick path (<= 73 registers), 6 for the stencils.
+template <bool kDerived>
+__global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
     const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned dense = 0, evald = 0;
-    if (hit) march_gather(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald);
+    if (hit) march_gather<kDerived>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         reinterpret_cast<float4*>(L.out)[pix] = px;
@@ -125,6 +137,7 @@ __global__ void __launch_bounds__(128) k_render_gather(const __grid_constant__ R
 // from one work queue spanning all views (each view: its own volume, uniforms,
 // transfer function, camera, output and size). A packet's view is found by
 // binary search over the views' packet prefix sums.
+template <bool kDerived>
 __global__ void __launch_bounds__(256) k_render_batch(const __grid_constant__ BatchLaunch B) {
     const int lane = threadIdx.x & 31;
     unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0;
@@ -153,9 +166,14 @@ __global__ void __launch_bounds__(256) k_render_batch(const __grid_constant__ Ba
         const bool hit = inside && setup_ray(vw.cam, vw.rc, i, j, v.n, v.s, r);
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned dense = 0, evald = 0;
-        if (hit)
-            march_gather(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out, dense,
-                         evald);
+        if (hit) {
+            if (kDerived && v.dbricks)
+                march_gather<true>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
+                                   dense, evald);
+            else
+                march_gather<false>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
+                                    dense, evald);
+        }
         if (inside) reinterpret_cast<float4*>(vw.out)[(long long)j * vw.W + i] = out;
         rays_hit += hit ? 1u : 0u;
         dense_tot += dense;
@@ -168,16 +186,21 @@ __global__ void __launch_bounds__(256) k_render_batch(const __grid_constant__ Ba
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st) {
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
-    k_render_gather<<<grid, 128, 0, st>>>(L);
+    if (L.vol.dbricks)
+        k_render_gather<true><<<grid, 128, 0, st>>>(L);
+    else
+        k_render_gather<false><<<grid, 128, 0, st>>>(L);
     return cudaGetLastError();
 }
 
+// The batched kernel takes each view's derived bricks when that volume has them
+// (one instantiation handles both, since a batch may mix volumes).
 cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch, warps_per_block * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch<true>, warps_per_block * 32, 0);
 }
 
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st) {
-    k_render_batch<<<ctas, warps_per_block * 32, 0, st>>>(B);
+    k_render_batch<true><<<ctas, warps_per_block * 32, 0, st>>>(B);
     return cudaGetLastError();
 }
 

@@ -187,6 +187,32 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
     out[9] = hyz;
 }
 
+// Sample field from derived bricks: trilinear interpolation of the 10 voxel-wise
+// channels over the cell's 8 corners (already in mm units). `cell` is the local
+// corner index of voxel (i0, j0, k0) within the brick's 9^3 block.
+__device__ __forceinline__ void field_eval_derived(const float4* __restrict__ brick, int cell, float fx, float fy,
+                                                   float fz, float out[10]) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) out[q] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+        const float4* p = brick + 3 * (cell + (dz * kDerEdge + dy) * kDerEdge + dx);
+        const float4 a = __ldg(p), m = __ldg(p + 1), t = __ldg(p + 2);
+        out[0] = fmaf(w, a.x, out[0]);
+        out[1] = fmaf(w, a.y, out[1]);
+        out[2] = fmaf(w, a.z, out[2]);
+        out[3] = fmaf(w, a.w, out[3]);
+        out[4] = fmaf(w, m.x, out[4]);
+        out[5] = fmaf(w, m.y, out[5]);
+        out[6] = fmaf(w, m.z, out[6]);
+        out[7] = fmaf(w, m.w, out[7]);
+        out[8] = fmaf(w, t.x, out[8]);
+        out[9] = fmaf(w, t.y, out[9]);
+    }
+}
+
 // Trilinear value only (the vesselness channel): 8 corner voxels of the cell.
 template <class Load>
 __device__ __forceinline__ float value_eval(const Load& load, int base, float fx, float fy, float fz) {
@@ -245,6 +271,9 @@ __device__ __forceinline__ void sample_optics(const float f[10], float vval, con
     const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
     const float wk = fminf(fmaxf(1.0f + tp.gamma * kappa / tp.kappa_ref, 0.0f), tp.w_max);
     alpha = fminf(fmaxf(tp.opacity_scale * c.w * mg * wk, 0.0f), 1.0f);
+    // optional step-size correction 1 - (1 - alpha)^e = -expm1(e log1p(-alpha)): accurate
+    // relative to alpha also for nearly transparent samples
+    if (tp.alpha_exp > 0.0f) alpha = -expm1f(tp.alpha_exp * log1pf(-alpha));
     if (tp.shading) {
         const float d = fabsf(fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2])));
         const float d2 = d * d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;

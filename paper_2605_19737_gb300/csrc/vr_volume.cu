@@ -154,6 +154,43 @@ __global__ void __launch_bounds__(256) k_make_bricks(const float* __restrict__ n
     }
 }
 
+// One CTA per brick: the voxel-wise intensity, central-difference gradient (Eq. 2)
+// and second/mixed differences (Sec. 2.3) of the brick's 9^3 corner voxels, with
+// clamp-to-edge neighbours, divided by the spacing -- the per-voxel morphology
+// the paper's compute shader produces, laid out for 16-byte loads.
+__global__ void __launch_bounds__(256) k_make_derived(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
+                                                      int nby, float hx, float hy, float hz, float* __restrict__ out) {
+    const long long b = blockIdx.x;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    const long long row = (long long)ny * nx;
+    for (int e = threadIdx.x; e < kDerEdge * kDerEdge * kDerEdge; e += blockDim.x) {
+        const int lx = e % kDerEdge, ly = (e / kDerEdge) % kDerEdge, lz = e / (kDerEdge * kDerEdge);
+        const int x = min(kCells * bx + lx, nx - 1), y = min(kCells * by + ly, ny - 1), z = min(kCells * bz + lz, nz - 1);
+        const int xm = max(x - 1, 0), xp = min(x + 1, nx - 1);
+        const int ym = max(y - 1, 0), yp = min(y + 1, ny - 1);
+        const int zm = max(z - 1, 0), zp = min(z + 1, nz - 1);
+        auto at = [&](int i, int j, int k) { return __ldg(norm + (long long)k * row + (long long)j * nx + i); };
+        const float c = at(x, y, z), c2 = 2.0f * c;
+        float4 a, m, t;
+        a.x = c;
+        a.y = (at(xp, y, z) - at(xm, y, z)) * (0.5f * hx);
+        a.z = (at(x, yp, z) - at(x, ym, z)) * (0.5f * hy);
+        a.w = (at(x, y, zp) - at(x, y, zm)) * (0.5f * hz);
+        m.x = (at(xp, y, z) - c2 + at(xm, y, z)) * (hx * hx);
+        m.y = (at(x, yp, z) - c2 + at(x, ym, z)) * (hy * hy);
+        m.z = (at(x, y, zp) - c2 + at(x, y, zm)) * (hz * hz);
+        m.w = ((at(xp, yp, z) - at(xp, ym, z)) - (at(xm, yp, z) - at(xm, ym, z))) * (0.25f * hx * hy);
+        t.x = ((at(xp, y, zp) - at(xp, y, zm)) - (at(xm, y, zp) - at(xm, y, zm))) * (0.25f * hx * hz);
+        t.y = ((at(x, yp, zp) - at(x, yp, zm)) - (at(x, ym, zp) - at(x, ym, zm))) * (0.25f * hy * hz);
+        t.z = 0.0f;
+        t.w = 0.0f;
+        float4* o = reinterpret_cast<float4*>(out + b * kDerBrickFloats) + 3 * e;
+        o[0] = a;
+        o[1] = m;
+        o[2] = t;
+    }
+}
+
 // One warp per brick: min/max of I_norm over the brick's corner voxels
 // [8b, min(8b+8, N-1)] per axis, quantised to qlo = floor(min*65535),
 // qhi = ceil(max*65535) (float32 round-to-nearest products).
@@ -289,6 +326,14 @@ cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[
     const long long nbr = (long long)nb[0] * nb[1] * nb[2];
     const unsigned blocks = (unsigned)((nbr + 7) / 8);
     k_brick_minmax<<<blocks, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], nbr, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], const float s[3], float* dbricks,
+                                cudaStream_t st) {
+    const long long nbr = (long long)nb[0] * nb[1] * nb[2];
+    k_make_derived<<<(unsigned)nbr, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], 1.0f / s[0], 1.0f / s[1],
+                                                  1.0f / s[2], dbricks);
     return cudaGetLastError();
 }
 

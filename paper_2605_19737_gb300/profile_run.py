@@ -1,6 +1,6 @@
 """Render a named workload a few times (for Nsight Compute captures and quick timing).
 
-    python -m paper_2605_19737_gb300.profile_run --workload brainweb_1080p --kernel staged --frames 3
+    python -m paper_2605_19737_gb300.profile_run --workload brainweb_1080p --kernel gather --frames 3
 
 Workloads: brainweb_1080p (181x217x181 uint16, 1920x1080), brainweb_540p (same
 volume, 960x540), head64 (64^3 float32, 128x128). Prints the mean frame time
@@ -24,7 +24,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="brainweb_1080p", choices=["brainweb_1080p", "brainweb_540p", "head64"])
-    ap.add_argument("--kernel", default="staged", choices=["gather", "staged"])
+    ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=8)
     ap.add_argument("--warps", type=int, default=4)
@@ -35,7 +35,8 @@ def main():
         case = workloads.brainweb_1080p(width=960, height=540)
     else:
         case = workloads.brainweb_1080p()
-    kernel = pkg.VR_KERNEL_STAGED if args.kernel == "staged" else pkg.VR_KERNEL_GATHER
+    kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
+              "stencil": pkg.VR_KERNEL_GATHER_STENCIL}[args.kernel]
     vol = case["volume"]
     data = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
     with pkg.Context(0) as ctx:

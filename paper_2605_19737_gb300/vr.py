@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libvr.so")
 VR_OK, VR_ERR_INVALID_ARG, VR_ERR_NOT_READY, VR_ERR_CUDA, VR_ERR_OOM, VR_ERR_TIMEOUT, VR_ERR_DEGENERATE = range(7)
 VR_F32, VR_U16 = 0, 1
 VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL = 0, 1, 2
-VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED = 0, 1, 2
+VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_NOT_READY", 3: "VR_ERR_CUDA", 4: "VR_ERR_OOM",
                 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_DEGENERATE"}
@@ -32,7 +32,7 @@ class vr_tissue_params(ctypes.Structure):
                 ("shading", ctypes.c_int), ("gamma", ctypes.c_float), ("kappa_ref", ctypes.c_float),
                 ("w_max", ctypes.c_float), ("ka", ctypes.c_float), ("kd", ctypes.c_float),
                 ("ks", ctypes.c_float), ("opacity_scale", ctypes.c_float), ("et_threshold", ctypes.c_float),
-                ("step_vox", ctypes.c_float)]
+                ("step_vox", ctypes.c_float), ("opacity_ref_step", ctypes.c_float)]
 
 
 class vr_counters(ctypes.Structure):

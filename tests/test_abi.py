@@ -50,8 +50,8 @@ def test_struct_layouts():
     assert ctypes.sizeof(vr.vr_camera) == 48
     assert ctypes.sizeof(vr.vr_counters) == 32
     assert ctypes.sizeof(vr.vr_render_opts) == 16
-    # 3 ints, pointer (8-aligned), 3 ints, 9 floats -> 12 + 4 pad + 8 + 12 + 36 = 72
-    assert ctypes.sizeof(vr.vr_tissue_params) == 72
+    # 3 ints, pointer (8-aligned), 3 ints, 10 floats -> 12 + 4 pad + 8 + 12 + 40 = 76 -> 80 (8-aligned)
+    assert ctypes.sizeof(vr.vr_tissue_params) == 80
 
 
 def test_null_context_is_rejected_without_gpu(libpath):

@@ -3,8 +3,12 @@ central finite differences of the GPU forward renderer, plus the autograd
 binding and a short transfer-function fit.
 
 Bars: normwise relative error <= 1e-3 per parameter group against the
-oracle (rays whose stopping sample is ambiguous carry no upstream gradient);
-directional finite differences of the FP32 forward within 1e-3 relative.
+oracle; rays whose stopping sample is ambiguous, or that pass within float32
+rounding of a point where the sample's opacity or colour has a kink (a
+transfer-function knot, a clamp; oracle FLAG_KINK), carry no upstream gradient
+-- there the two one-sided derivatives are both correct -- and they are at most
+5% of the rays. Directional finite differences of the FP32 forward within 1e-3
+relative.
 """
 
 import numpy as np
@@ -56,11 +60,12 @@ def _cases():
                                        for az, el in ((30, 20), (150, -25))]))
     small["params"] = dict(small["params"], gamma=0.4, kappa_ref=0.1, w_max=3.0)
     bw = workloads.scaled_brainweb((41, 47, 39), width=44, height=36, n_cams=2)
-    return {"head_1d": small, "brainweb_2d": bw}
+    corr = dict(small, params=dict(small["params"], opacity_ref_step=0.7, step_vox=0.4))
+    return {"head_1d": small, "brainweb_2d": bw, "head_1d_corrected": corr}
 
 
-@pytest.mark.parametrize("kernel", [0, 2])  # per-lane global atomics (default), brick-synchronous
-@pytest.mark.parametrize("name", ["head_1d", "brainweb_2d"])
+@pytest.mark.parametrize("kernel", [0, 2, 3])  # per-lane (derived bricks), brick-synchronous, per-lane stencils
+@pytest.mark.parametrize("name", ["head_1d", "brainweb_2d", "head_1d_corrected"])
 def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     case = _cases()[name]
     In32 = oracle.normalize(case["volume"]).astype(np.float32)
@@ -72,7 +77,8 @@ def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     dl = rng.normal(size=(n, H, W, 4))
     P = oracle_params(case["params"], case["tf"])
     fwd = oracle.render(In, case["spacing"], P, case["tf"], case["cams"], W, H, gmax_value=gmax, alternatives=False)
-    amb = (fwd.flags & (oracle.FLAG_ET | oracle.FLAG_COUNT)) != 0
+    amb = (fwd.flags & (oracle.FLAG_ET | oracle.FLAG_COUNT | oracle.FLAG_KINK)) != 0
+    assert amb.mean() <= 0.05
     dl[amb] = 0.0
     dtf_o, dpar_o, dvol_o = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H, dl,
                                                gmax_value=gmax)
@@ -129,20 +135,22 @@ def test_backward_matches_gpu_finite_differences(vr, torch):
         rp = float(np.float32(pp[name])) - float(np.float32(pm[name]))
         fd = (loss(params=pp) - loss(params=pm)) / rp
         assert fd == pytest.approx(dpar[idx], rel=5 * TOL_GRAD, abs=1e-3 * np.abs(dpar).max()), name
-    # voxels (normalised intensities; |grad I|max held fixed by the library), on a
-    # kink-free configuration: linear transfer function, no curvature term, no
-    # shading (their kinks make a finite voxel step one-sided; the oracle comparison
-    # covers those terms)
+    # voxels (normalised intensities), on a configuration smooth in the voxels:
+    # linear transfer function, no curvature term, no shading, no gradient-magnitude
+    # modulation. |grad I| is a cone at grad I = 0, and a white-noise voxel step
+    # moves the gradient of the many low-|grad I| samples by a comparable amount, so
+    # with those terms on, the central difference is off by ~1e-3 at any step that
+    # float32 resolves (the oracle comparison above covers those terms)
     case["tf"] = np.zeros_like(case["tf"])
     x = np.arange(case["tf"].shape[1], dtype=np.float32) / (case["tf"].shape[1] - 1)
     case["tf"][0, :, 0], case["tf"][0, :, 1], case["tf"][0, :, 2] = 0.2 + 0.6 * x, 0.9 - 0.5 * x, 0.5
     case["tf"][0, :, 3] = 0.01 + 0.12 * x
-    case["params"] = dict(case["params"], gamma=0.0, shading=0)
+    case["params"] = dict(case["params"], gamma=0.0, shading=0, grad_mod=0)
     vr.set_normalized(vid, torch.from_numpy(In32).cuda())
     vr.set_tissue_params(vid, case["tf"], **case["params"])
     _, _, dvol = [x.cpu().numpy().astype(np.float64) for x in vr.render_backward(vid, case["cams"], W, H, dl)]
     u = rng.normal(size=In32.shape)
-    h = 3e-4
+    h = 3e-3
     vp = torch.from_numpy((In32 + h * u).astype(np.float32)).cuda()
     vm = torch.from_numpy((In32 - h * u).astype(np.float32)).cuda()
     step = (vp.double() - vm.double()).cpu().numpy()

@@ -90,7 +90,7 @@ def test_classification_bit_exact(vr, torch):
     vr.free_volume(vid)
 
 
-KERNELS = [1, 2]  # VR_KERNEL_GATHER, VR_KERNEL_STAGED
+KERNELS = [1, 2, 3]  # VR_KERNEL_GATHER (derived bricks), VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -145,6 +145,19 @@ def test_anisotropic_spacing_grad_mod(vr, torch, kernel):
     vr.free_volume(vid)
 
 
+@pytest.mark.parametrize("step", [0.5, 0.3])
+def test_opacity_correction_parity(vr, torch, step):
+    """Step-size opacity correction against the oracle (off by default; Eqs. 5-6 literal)."""
+    case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
+    case["params"] = dict(case["params"], step_vox=step, opacity_ref_step=0.8)
+    vid = _load_case(vr, torch, case)
+    img, rs = _render(vr, torch, vid, case)
+    _, empty = vr.get_bricks(vid)
+    res = oracle_render_case(case, brick_empty=empty)
+    assert_rgba_parity(img, res, what="opacity correction")
+    vr.free_volume(vid)
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_skip_is_bit_neutral_and_deterministic(vr, torch, kernel):
     case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
@@ -162,10 +175,11 @@ def test_skip_is_bit_neutral_and_deterministic(vr, torch, kernel):
 @pytest.mark.parametrize("packet_w,warps", [(8, 4), (4, 8), (16, 2), (32, 1), (8, 8)])
 def test_staged_equals_gather_bitwise(vr, torch, packet_w, warps):
     """Brick staging changes only where voxels are read from, never the arithmetic:
-    images and per-ray sample counts are bit-identical for every packet shape."""
+    images and per-ray sample counts equal the per-lane stencil kernel's bit for bit,
+    for every packet shape."""
     case = workloads.scaled_brainweb((61, 73, 59), width=100, height=75, n_cams=3)
     vid = _load_case(vr, torch, case)
-    a, ra = _render(vr, torch, vid, case, kernel=1)
+    a, ra = _render(vr, torch, vid, case, kernel=3)
     b, rb = _render(vr, torch, vid, case, kernel=2, packet_w=packet_w, warps_per_block=warps)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(ra, rb)

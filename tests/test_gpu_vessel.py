@@ -55,7 +55,7 @@ def _vessel_case(dims, W, H, seed=52):
     return case
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_vessel_render_parity(vr, torch, kernel):
     case = _vessel_case((48, 44, 40), 96, 80)
     vid = vr.load_volume(torch.from_numpy(case["volume"]).cuda())

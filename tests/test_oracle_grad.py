@@ -84,3 +84,66 @@ def test_gradient_zero_where_transparent():
     assert np.all(dIn == 0.0)
     assert np.all(dtf[..., :3] == 0.0) and np.abs(dtf[..., 3]).max() > 0
     assert dpar[0] == 0.0 and dpar[4] == 0.0
+
+
+
+def _flat_case(In, tf_w, **over):
+    dims = In.shape[::-1]
+    sp = (1.0, 1.0, 1.0)
+    cams = ph.camera_array([ph.orbit_camera(dims, sp, 30, 20, width=8, height=6)])
+    tf = np.random.default_rng(3).random((1, tf_w, 4)).astype(np.float32)
+    pars = dict(tf_mode=0, tf_w=tf_w, tf_h=1, grad_mod=0, shading=0, gamma=0.0, kappa_ref=1.0, w_max=3.0, ka=0.3,
+                kd=0.6, ks=0.2, opacity_scale=0.5, et_threshold=2.0, step_vox=0.5)
+    pars.update(over)
+    r = oracle.render(In, sp, _P(pars), tf, cams, 8, 6, gmax_value=1.0, alternatives=False)
+    hit = r.dense > 0
+    assert hit.sum() > 10
+    return hit, (r.flags & oracle.FLAG_KINK) != 0
+
+
+@pytest.mark.parametrize("level,flagged", [(128.0 / 255.0 + 1e-8, True), (128.5 / 255.0, False)])
+def test_kink_flag_marks_transfer_function_knots(level, flagged):
+    """A homogeneous volume whose intensity sits within rounding of a transfer-function
+    knot puts every sample of every hit ray on the knot, where the opacity has two
+    one-sided derivatives in the voxels: every hit ray carries FLAG_KINK; half an
+    entry away none does. (The gradient is exactly zero there, which is not flagged.)"""
+    hit, k = _flat_case(np.full((7, 8, 9), level), 256)
+    assert np.all(k[hit]) if flagged else not np.any(k)
+
+
+def _ray_ux(cam, W, H, i, j, dims, dt):
+    """x voxel coordinates u = p/s - 0.5 of the samples of pixel (i, j), unit spacing."""
+    cam = np.asarray(cam, np.float64).reshape(12)
+    a, b = 2.0 * (i + 0.5) / W - 1.0, 1.0 - 2.0 * (j + 0.5) / H
+    d = cam[3:6] + a * cam[6:9] + b * cam[9:12]
+    d /= np.linalg.norm(d)
+    o = cam[0:3]
+    t0 = max(min((0.0 - o[q]) / d[q], (dims[q] - o[q]) / d[q]) for q in range(3))
+    t1 = min(max((0.0 - o[q]) / d[q], (dims[q] - o[q]) / d[q]) for q in range(3))
+    t0 = max(t0, 0.0)
+    ks = np.arange(max(0, int(np.ceil((t1 - t0) / dt)) + 1))
+    t = t0 + (ks + 0.5) * dt
+    return o[0] + t[t < t1] * d[0] - 0.5
+
+
+@pytest.mark.parametrize("w_max,flagged", [(1.0 + 1e-5, True), (1.5, False)])
+def test_kink_flag_marks_curvature_clamp(w_max, flagged):
+    """A linear ramp along x has H = 0 away from the x faces (where clamp-to-edge
+    bends it), so kappa = 0 and w(kappa) = clamp(1, 0, w_max) at every sample whose
+    cell lies inside 1 <= u_x <= nx - 2: with w_max within 1e-4 of 1 exactly the rays
+    with such a sample are flagged; with w_max = 1.5 none is (a two-entry transfer
+    function has no interior knot)."""
+    nz, ny, nx = 7, 8, 9
+    In = np.broadcast_to(0.2 + 0.6 * np.arange(nx) / (nx - 1), (nz, ny, nx)).copy()
+    hit, k = _flat_case(In, 2, gamma=0.5, w_max=w_max)
+    if not flagged:
+        assert not np.any(k)
+        return
+    cam = ph.camera_array([ph.orbit_camera((nx, ny, nz), (1.0, 1.0, 1.0), 30, 20, width=8, height=6)])[0]
+    want = np.zeros_like(k)
+    for j in range(6):
+        for i in range(8):
+            if hit[0, j, i]:
+                ux = _ray_ux(cam, 8, 6, i, j, (nx, ny, nz), 0.5)
+                want[0, j, i] = np.any((ux >= 1.0) & (ux <= nx - 2.0))
+    assert want.sum() > 10 and np.array_equal(k, want)
