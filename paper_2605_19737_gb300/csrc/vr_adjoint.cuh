@@ -17,11 +17,22 @@ struct ParamGrad {
     float gamma, ka, kd, ks, os;
 };
 
-// Transfer-function gradient sink: shared-memory table (1D) or global atomics.
+// Transfer-function gradient sink: a shared-memory table (1D; scalar shared
+// atomics) or a global one (one 16-byte vector atomic per RGBA entry).
 struct TfGradSink {
     float* p;
-    __device__ __forceinline__ void add(int idx, float v) const {
-        if (v != 0.0f) atomicAdd(p + idx, v);
+    bool shared;
+    __device__ __forceinline__ void add4(int entry, float w, const float d[4]) const {
+        const float4 v = make_float4(w * d[0], w * d[1], w * d[2], w * d[3]);
+        if (shared) {
+            float* e = p + 4 * entry;
+            if (v.x != 0.0f) atomicAdd(e, v.x);
+            if (v.y != 0.0f) atomicAdd(e + 1, v.y);
+            if (v.z != 0.0f) atomicAdd(e + 2, v.z);
+            if (v.w != 0.0f) atomicAdd(e + 3, v.w);
+        } else if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) {
+            atomicAdd(reinterpret_cast<float4*>(p) + entry, v);
+        }
     }
 };
 
@@ -116,23 +127,22 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
     float dI = 0.f;
     const float T00a[4] = {T00.x, T00.y, T00.z, T00.w}, T01a[4] = {T01.x, T01.y, T01.z, T01.w};
     if (h == 1) {
+        dtf.add4(j, 1.0f - t, dr);
+        dtf.add4(j + 1, t, dr);
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-            dtf.add(4 * j + ch, (1.0f - t) * dr[ch]);
-            dtf.add(4 * (j + 1) + ch, t * dr[ch]);
+        for (int ch = 0; ch < 4; ++ch)
             if (in_x) dI = fmaf(dr[ch], (T01a[ch] - T00a[ch]) * (float)(w - 1), dI);
-        }
     } else {
         const float T10a[4] = {T10.x, T10.y, T10.z, T10.w}, T11a[4] = {T11.x, T11.y, T11.z, T11.w};
         const bool in_y = y >= 0.0f && y <= 1.0f;
         float dy = 0.f;
-        const int e00 = 4 * (k * w + j), e10 = 4 * ((k + 1) * w + j);
+        const int e00 = k * w + j, e10 = (k + 1) * w + j;
+        dtf.add4(e00, (1.0f - q) * (1.0f - t), dr);
+        dtf.add4(e00 + 1, (1.0f - q) * t, dr);
+        dtf.add4(e10, q * (1.0f - t), dr);
+        dtf.add4(e10 + 1, q * t, dr);
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-            dtf.add(e00 + ch, (1.0f - q) * (1.0f - t) * dr[ch]);
-            dtf.add(e00 + 4 + ch, (1.0f - q) * t * dr[ch]);
-            dtf.add(e10 + ch, q * (1.0f - t) * dr[ch]);
-            dtf.add(e10 + 4 + ch, q * t * dr[ch]);
             if (in_x)
                 dI = fmaf(dr[ch], ((1.0f - q) * (T01a[ch] - T00a[ch]) + q * (T11a[ch] - T10a[ch])) * (float)(w - 1),
                           dI);

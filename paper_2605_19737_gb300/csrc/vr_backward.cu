@@ -52,6 +52,101 @@ __device__ __forceinline__ void eval_field(const VolumeDev& v, long long bi, con
     }
 }
 
+// Adjoint of field_eval_derived: the sample's field gradient dfs (I, g, H in the
+// derived channels' mm units), trilinearly weighted, into the per-voxel channel
+// gradients of the cell's 8 corners -- three vector atomics per corner.
+__device__ __forceinline__ void scatter_channels(float* __restrict__ dgrad, const int n[3], const int i0[3],
+                                                 const float f[3], const float dfs[10]) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) any |= dfs[q] != 0.0f;
+    if (!any) return;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
+        if (w == 0.0f) continue;
+        const long long p = ((long long)(i0[2] + dz) * n[1] + (i0[1] + dy)) * n[0] + (i0[0] + dx);
+        float* g = dgrad + p * kDerFloats;
+        atomicAdd(reinterpret_cast<float4*>(g), make_float4(w * dfs[0], w * dfs[1], w * dfs[2], w * dfs[3]));
+        atomicAdd(reinterpret_cast<float4*>(g + 4), make_float4(w * dfs[4], w * dfs[5], w * dfs[6], w * dfs[7]));
+        atomicAdd(reinterpret_cast<float2*>(g + 8), make_float2(w * dfs[8], w * dfs[9]));
+    }
+}
+
+// Voxel p's channels read I at clamp(p +- 1) per axis. For voxel v, the p whose
+// "+1" (s = 0) or "-1" (s = 1) neighbour along an axis of size nn clamps to v.
+__device__ __forceinline__ int clamp_sources(int v, int nn, int sgn, int out[2]) {
+    int m = 0;
+    if (sgn == 0) {  // clamp(p + 1) == v
+        if (v >= 1) out[m++] = v - 1;
+        if (v == nn - 1) out[m++] = v;
+    } else {  // clamp(p - 1) == v
+        if (v <= nn - 2) out[m++] = v + 1;
+        if (v == 0) out[m++] = v;
+    }
+    return m;
+}
+
+// dL/dI[v] from the channel gradients: the transpose of the derived channels'
+// clamp-to-edge difference stencils (I; g_a = (I[p+a] - I[p-a]) / (2 s_a);
+// H_aa = (I[p+a] - 2 I[p] + I[p-a]) / s_a^2; H_ab = the four (p +- a +- b)
+// corners / (4 s_a s_b)), gathered per voxel (no atomics).
+__global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restrict__ G, int nx, int ny, int nz,
+                                                            float sx, float sy, float sz, float* __restrict__ dvol) {
+    const long long nvox = (long long)nx * ny * nz;
+    const int nn[3] = {nx, ny, nz};
+    const float sp[3] = {sx, sy, sz};
+    const int hidx[3][3] = {{4, 7, 8}, {7, 5, 9}, {8, 9, 6}};  // channel of H_ab
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nvox;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v[3] = {(int)(e % nx), (int)((e / nx) % ny), (int)(e / ((long long)nx * ny))};
+        auto at = [&](const int p[3], int ch) {
+            return __ldg(G + (((long long)p[2] * ny + p[1]) * nx + p[0]) * kDerFloats + ch);
+        };
+        float acc = at(v, 0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float cg = 0.5f / sp[a], ch = 1.0f / (sp[a] * sp[a]);
+            acc -= 2.0f * ch * at(v, 4 + a);
+#pragma unroll
+            for (int sg = 0; sg < 2; ++sg) {
+                int src[2];
+                const int m = clamp_sources(v[a], nn[a], sg, src);
+                for (int u = 0; u < m; ++u) {
+                    int p[3] = {v[0], v[1], v[2]};
+                    p[a] = src[u];
+                    acc += (sg == 0 ? cg : -cg) * at(p, 1 + a) + ch * at(p, 4 + a);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < 3; ++b) {
+                const float cm = 0.25f / (sp[a] * sp[b]);
+#pragma unroll
+                for (int sa = 0; sa < 2; ++sa) {
+#pragma unroll
+                    for (int sb = 0; sb < 2; ++sb) {
+                        int pa[2], pb[2];
+                        const int ma = clamp_sources(v[a], nn[a], sa, pa), mb = clamp_sources(v[b], nn[b], sb, pb);
+                        const float sgn = (sa == sb) ? cm : -cm;
+                        for (int ua = 0; ua < ma; ++ua)
+                            for (int ub = 0; ub < mb; ++ub) {
+                                int p[3] = {v[0], v[1], v[2]};
+                                p[a] = pa[ua];
+                                p[b] = pb[ub];
+                                acc += sgn * at(p, hidx[a][b]);
+                            }
+                    }
+                }
+            }
+        }
+        dvol[e] = acc;
+    }
+}
+
 template <bool kDerived>
 __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     extern __shared__ float s_dtf[];
@@ -66,7 +161,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
     // same hot entries do not serialise on one address.
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    const TfGradSink sink{tf_dst};
+    const TfGradSink sink{tf_dst, B.tf_in_smem != 0};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
@@ -152,7 +247,9 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
                 const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
                 float dfs[10];
                 sample_adjoint(fld, vval, r.dir, L.tp, tf, inv_gmax, da, dc, sink, dp, dfs);
-                if (B.dvol) {
+                if (kDerived && B.dgrad) {
+                    scatter_channels(B.dgrad, v.n, i0, f, dfs);
+                } else if (B.dvol) {
                     const int x0 = i0[0] - 1, y0 = i0[1] - 1, z0 = i0[2] - 1;
                     const int nx = v.n[0], ny = v.n[1], nz = v.n[2];
                     float* dv = B.dvol;
@@ -218,7 +315,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     __syncthreads();
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    const TfGradSink sink{tf_dst};
+    const TfGradSink sink{tf_dst, B.tf_in_smem != 0};
     const int i = blockIdx.x * 16 + (warp & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (l >> 3);
     const int cam = blockIdx.z;
@@ -407,6 +504,15 @@ __global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ co
 }
 
 }  // namespace
+
+cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
+                                      cudaStream_t st) {
+    const long long nvox = (long long)n[0] * n[1] * n[2];
+    const long long blocks = (nvox + 255) / 256;
+    k_channels_to_voxels<<<(unsigned)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, st>>>(dgrad, n[0], n[1], n[2],
+                                                                                          s[0], s[1], s[2], dvol);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st) {
     const long long blocks = (n + 255) / 256;

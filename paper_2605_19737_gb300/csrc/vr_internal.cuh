@@ -101,6 +101,7 @@ struct BackwardLaunch {
     int tf_in_smem;         // 1: sum 1D transfer-function gradients in shared memory first
     float* dtf_copies;      // else: n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
     int n_copies;
+    float* dgrad;           // derived-brick path with dvol: zeroed nvox x kDerFloats channel gradients, else nullptr
 };
 
 constexpr int kTfGradCopies = 64;
@@ -165,6 +166,8 @@ cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
 cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st);
 // dtf[e] = sum over c of copies[c * n + e]
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
+cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
+                                      cudaStream_t st);
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st);
 cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
