@@ -18,12 +18,22 @@ struct ParamGrad {
 };
 
 // Transfer-function gradient sink: a shared-memory table (1D; scalar shared
-// atomics) or a global one (one 16-byte vector atomic per RGBA entry).
+// atomics) or a global one (one 16-byte vector atomic per RGBA entry). A lane's
+// consecutive samples mostly look up the same transfer-function cell, so the sink
+// accumulates the cell's (2 or 4) entry gradients in registers and writes them
+// out only when the cell changes (and once at the end of the ray: flush()).
 struct TfGradSink {
     float* p;
     bool shared;
-    __device__ __forceinline__ void add4(int entry, float w, const float d[4]) const {
-        const float4 v = make_float4(w * d[0], w * d[1], w * d[2], w * d[3]);
+    int w;          // entries per row
+    bool two_d;
+    int key = -1;   // first entry of the pending cell, -1 = none
+    float4 a00, a01, a10, a11;
+
+    __device__ __forceinline__ TfGradSink(float* p_, bool shared_, int w_, bool two_d_)
+        : p(p_), shared(shared_), w(w_), two_d(two_d_) {}
+
+    __device__ __forceinline__ void put(int entry, const float4& v) const {
         if (shared) {
             float* e = p + 4 * entry;
             if (v.x != 0.0f) atomicAdd(e, v.x);
@@ -34,13 +44,43 @@ struct TfGradSink {
             atomicAdd(reinterpret_cast<float4*>(p) + entry, v);
         }
     }
+    __device__ __forceinline__ void flush() {
+        if (key < 0) return;
+        put(key, a00);
+        put(key + 1, a01);
+        if (two_d) {
+            put(key + w, a10);
+            put(key + w + 1, a11);
+        }
+        key = -1;
+    }
+    // Add the bilinear weights (w00 .. w11) times d to cell `e00` (= k * w + j).
+    __device__ __forceinline__ void add_cell(int e00, float w00, float w01, float w10, float w11, const float d[4]) {
+        if (e00 != key) {
+            flush();
+            key = e00;
+            a00 = a01 = a10 = a11 = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        auto acc = [&](float4& a, float c) {
+            a.x = fmaf(c, d[0], a.x);
+            a.y = fmaf(c, d[1], a.y);
+            a.z = fmaf(c, d[2], a.z);
+            a.w = fmaf(c, d[3], a.w);
+        };
+        acc(a00, w00);
+        acc(a01, w01);
+        if (two_d) {
+            acc(a10, w10);
+            acc(a11, w11);
+        }
+    }
 };
 
 // dfield receives dL/d(I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz) in the same
 // (spacing-scaled) units as the sample field f.
 __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, const float dir[3], const TissueDev& tp,
                                                const float4* __restrict__ tf, float inv_gmax, float da,
-                                               const float dc[3], const TfGradSink& dtf, ParamGrad& dp,
+                                               const float dc[3], TfGradSink& dtf, ParamGrad& dp,
                                                float dfield[10]) {
     const float gx = f[1], gy = f[2], gz = f[3];
     const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
@@ -127,8 +167,7 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
     float dI = 0.f;
     const float T00a[4] = {T00.x, T00.y, T00.z, T00.w}, T01a[4] = {T01.x, T01.y, T01.z, T01.w};
     if (h == 1) {
-        dtf.add4(j, 1.0f - t, dr);
-        dtf.add4(j + 1, t, dr);
+        dtf.add_cell(j, 1.0f - t, t, 0.0f, 0.0f, dr);
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch)
             if (in_x) dI = fmaf(dr[ch], (T01a[ch] - T00a[ch]) * (float)(w - 1), dI);
@@ -136,11 +175,8 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
         const float T10a[4] = {T10.x, T10.y, T10.z, T10.w}, T11a[4] = {T11.x, T11.y, T11.z, T11.w};
         const bool in_y = y >= 0.0f && y <= 1.0f;
         float dy = 0.f;
-        const int e00 = k * w + j, e10 = (k + 1) * w + j;
-        dtf.add4(e00, (1.0f - q) * (1.0f - t), dr);
-        dtf.add4(e00 + 1, (1.0f - q) * t, dr);
-        dtf.add4(e10, q * (1.0f - t), dr);
-        dtf.add4(e10 + 1, q * t, dr);
+        const int e00 = k * w + j;
+        dtf.add_cell(e00, (1.0f - q) * (1.0f - t), (1.0f - q) * t, q * (1.0f - t), q * t, dr);
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
             if (in_x)

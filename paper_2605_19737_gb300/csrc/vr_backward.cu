@@ -16,11 +16,15 @@
 //        dL/dalpha_k = T_k (<dL/dC, c_k - R_{k+1}> + dL/dA P_k),
 //        dL/dc_k     = T_k alpha_k dL/dC              (Eqs. 5-6 differentiated);
 //   3. sample_adjoint / field_adjoint_scatter chain these to the parameters.
-// Transfer-function gradients of a 1D table are summed in shared memory per CTA
-// and flushed with one atomic per non-zero entry; a 2D table is summed into 64
-// private global copies (CTA c into copy c % 64) that k_sum_copies adds up
-// afterwards -- contended atomics on one 256 KB table cost 10x the rest of the
-// kernel; voxels use global atomics; uniform gradients are warp-reduced first.
+// Transfer-function gradients are accumulated per lane while its samples stay in
+// one transfer-function cell; a 1D table is then summed in shared memory per CTA
+// and flushed with one atomic per non-zero entry; a 2D table is summed with
+// 16-byte vector atomics into 64 private global copies (CTA c into copy c % 64)
+// that k_sum_copies adds up afterwards -- contended atomics on one 256 KB table
+// cost 10x the rest of the kernel. Voxel gradients: on the derived bricks, per-
+// voxel channel gradients (vector atomics) and a gather pass through the stencil
+// transposes; otherwise scalar global atomics on the voxels. Uniform gradients are
+// warp-reduced first.
 #include "vr_adjoint.cuh"
 
 namespace vr {
@@ -147,8 +151,10 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
     }
 }
 
+// 4 resident CTAs per SM (<= 128 registers): measured 1 ms faster at 1080p than
+// the 3 that the unbounded register count allows.
 template <bool kDerived>
-__global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__ BackwardLaunch B) {
+__global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     extern __shared__ float s_dtf[];
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
     // same hot entries do not serialise on one address.
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    const TfGradSink sink{tf_dst, B.tf_in_smem != 0};
+    TfGradSink sink(tf_dst, B.tf_in_smem != 0, L.tp.tf_w, L.tp.tf_h > 1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
@@ -268,6 +274,7 @@ __global__ void __launch_bounds__(128) k_render_backward(const __grid_constant__
             }
         }
     }
+    sink.flush();
     // uniform gradients: warp sums, one atomic per warp and parameter
     float pv[5] = {dp.gamma, dp.ka, dp.kd, dp.ks, dp.os};
 #pragma unroll
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     __syncthreads();
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    const TfGradSink sink{tf_dst, B.tf_in_smem != 0};
+    TfGradSink sink(tf_dst, B.tf_in_smem != 0, L.tp.tf_w, L.tp.tf_h > 1);
     const int i = blockIdx.x * 16 + (warp & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (l >> 3);
     const int cam = blockIdx.z;
@@ -475,6 +482,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
             __syncwarp();
         }
     }
+    sink.flush();
     float pv[5] = {dp.gamma, dp.ka, dp.kd, dp.ks, dp.os};
 #pragma unroll
     for (int e = 0; e < 5; ++e) {
