@@ -84,17 +84,18 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
                                                float dfield[10]) {
     const float gx = f[1], gy = f[2], gz = f[3];
     const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, Hgx = 0.f, Hgy = 0.f, Hgz = 0.f;
+    // forward values with sample_optics' exact arithmetic (same clamp decisions)
+    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, Hgx = 0.f, Hgy = 0.f, Hgz = 0.f, r = 0.f;
     if (gg > 0.0f) {
-        gmag = sqrtf(gg);
+        r = rsqrtf(gg);
+        gmag = gg * r;
         Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
         Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
         Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
-        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) / gg;
-        const float inv = 1.0f / gmag;
-        hx = gx * inv;
-        hy = gy * inv;
-        hz = gz * inv;
+        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) * (r * r);
+        hx = gx * r;
+        hy = gy * r;
+        hz = gz * r;
     }
     const float gn = gmag * inv_gmax;
     const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
@@ -123,7 +124,7 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
         c = lerp4(lerp4(T00, T01, t), lerp4(T10, T11, t), q);
     }
     const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
-    const float wi = 1.0f + tp.gamma * kappa / tp.kappa_ref;
+    const float wi = fmaf(tp.gk, kappa, 1.0f);
     const float wk = fminf(fmaxf(wi, 0.0f), tp.w_max);
     const float raw = tp.opacity_scale * c.w * mg * wk;
     const float dot = fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2]));
@@ -159,8 +160,8 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
     const float dmg = draw * tp.opacity_scale * c.w * wk;
     const float dw = draw * tp.opacity_scale * c.w * mg;
     const float dwi = (wi >= 0.0f && wi <= tp.w_max) ? dw : 0.0f;
-    dp.gamma += dwi * kappa / tp.kappa_ref;
-    const float dkappa = dwi * tp.gamma / tp.kappa_ref;
+    dp.gamma += dwi * kappa * tp.inv_kref;
+    const float dkappa = dwi * tp.gk;
     float dgn = (tp.grad_mod && gn < 1.0f) ? dmg : 0.0f;
     // transfer-function lookup
     const bool in_x = I >= 0.0f && I <= 1.0f;
@@ -197,15 +198,14 @@ __device__ __forceinline__ void sample_adjoint(const float f[10], float vval, co
             const float sgn = dot > 0.0f ? 1.0f : (dot < 0.0f ? -1.0f : 0.0f);
             const float ax = dd * sgn * dir[0], ay = dd * sgn * dir[1], az = dd * sgn * dir[2];
             const float proj = fmaf(ax, hx, fmaf(ay, hy, az * hz));
-            const float inv = 1.0f / gmag;
-            dgx += (ax - proj * hx) * inv;
-            dgy += (ay - proj * hy) * inv;
-            dgz += (az - proj * hz) * inv;
+            dgx += (ax - proj * hx) * r;
+            dgy += (ay - proj * hy) * r;
+            dgz += (az - proj * hz) * r;
         }
         dgx = fmaf(dgn * inv_gmax, hx, dgx);
         dgy = fmaf(dgn * inv_gmax, hy, dgy);
         dgz = fmaf(dgn * inv_gmax, hz, dgz);
-        const float s = dkappa / gg;
+        const float s = dkappa * (r * r);
         dgx = fmaf(2.0f * s, Hgx - kappa * gx, dgx);
         dgy = fmaf(2.0f * s, Hgy - kappa * gy, dgy);
         dgz = fmaf(2.0f * s, Hgz - kappa * gz, dgz);

@@ -450,6 +450,8 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
     d.tf_mode = tp->tf_mode, d.tf_w = tp->tf_w, d.tf_h = tp->tf_h;
     d.grad_mod = tp->grad_mod, d.shading = tp->shading;
     d.gamma = tp->gamma, d.kappa_ref = tp->kappa_ref, d.w_max = tp->w_max;
+    d.gk = (float)((double)tp->gamma / (double)tp->kappa_ref);
+    d.inv_kref = (float)(1.0 / (double)tp->kappa_ref);
     d.ka = tp->ka, d.kd = tp->kd, d.ks = tp->ks;
     d.opacity_scale = tp->opacity_scale, d.et_threshold = tp->et_threshold, d.step_vox = tp->step_vox;
     {

@@ -38,6 +38,7 @@ struct TissueDev {
     int tf_mode, tf_w, tf_h, grad_mod, shading;
     float gamma, kappa_ref, w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox;
     float alpha_exp;  // dt / opacity_ref_step for the step-size opacity correction; 0 = off
+    float gk, inv_kref;  // gamma / kappa_ref and 1 / kappa_ref (rounded from double on the host)
 };
 
 // Per-volume constants that kernels read from device memory (so that host code

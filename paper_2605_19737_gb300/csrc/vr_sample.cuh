@@ -255,21 +255,22 @@ __device__ __forceinline__ void sample_optics(const float f[10], float vval, con
     const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
     if (gg > 0.0f) {
-        gmag = sqrtf(gg);
+        // one reciprocal square root gives |g|, the unit normal and 1/|g|^2
+        const float r = rsqrtf(gg);
+        gmag = gg * r;
         const float Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
         const float Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
         const float Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
-        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) / gg;
-        const float inv = 1.0f / gmag;
-        hx = gx * inv;
-        hy = gy * inv;
-        hz = gz * inv;
+        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) * (r * r);
+        hx = gx * r;
+        hy = gy * r;
+        hz = gz * r;
     }
     const float gn = gmag * inv_gmax;
     const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
     const float4 c = tf_lookup(tf, tp.tf_w, tp.tf_h, f[0], y);
     const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
-    const float wk = fminf(fmaxf(1.0f + tp.gamma * kappa / tp.kappa_ref, 0.0f), tp.w_max);
+    const float wk = fminf(fmaxf(fmaf(tp.gk, kappa, 1.0f), 0.0f), tp.w_max);
     alpha = fminf(fmaxf(tp.opacity_scale * c.w * mg * wk, 0.0f), 1.0f);
     // optional step-size correction 1 - (1 - alpha)^e = -expm1(e log1p(-alpha)): accurate
     // relative to alpha also for nearly transparent samples
