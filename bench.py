@@ -12,8 +12,13 @@ A step is one frame: one vr_render call over the resident volume.
   e2e    the same metric through the C ABI with host buffers: per frame the
          tissue uniforms and transfer function are uploaded from host memory
          and the image is copied back to pinned host memory.
-Run `python bench.py --impl reference` for the FP64 CPU oracle on the same
-workload (a bounded sample of the frame).
+Also reported (not timed in the step): fps_wall (vr_render wall clock, launch
+included), fwd+bwd on the same 1080p view, fwd+bwd over the 8 views of the
+differentiable 128^3 workload, the batched persistent render (4 volumes x 64
+cameras, CUDA graph), the vesselness precompute, time to first pixel, and the
+roofline of the forward kernel against a measured FP32 FMA peak. --fit adds the
+200-step transfer-function fit. Run `python bench.py --impl reference` for the
+FP64 CPU oracle on the same workload (a bounded sample of the frame).
 """
 
 import argparse
@@ -164,6 +169,48 @@ def run_reference(args):
                                             "d2h_bytes_per_step": 0}})
 
 
+def fwd_bwd_multiview(ctx, dev, flush, args):
+    """Forward + backward over the 8 views of the differentiable workload (128^3 head,
+    512x512): transfer-function, uniform and voxel gradients, as one fit step
+    computes them (without the optimiser)."""
+    import torch
+
+    import paper_2605_19737_gb300 as pkg
+    from phantoms import workloads as wl
+    case = wl.diff_head128_8cam()
+    W, H, cams = case["W"], case["H"], case["cams"]
+    vid = ctx.load_volume(torch.from_numpy(case["volume"]).to(dev), case["spacing"])
+    ctx.precompute_morphology(vid)
+    ctx.set_tissue_params(vid, case["tf"], **case["params"])
+    out = torch.empty((cams.shape[0], H, W, 4), device=dev)
+    ctr = pkg.new_counters(dev.index or 0)
+    ctx.render(vid, cams, W, H, out=out, counters=ctr)
+    torch.cuda.synchronize()
+    dense = int(ctr.cpu().numpy()[1])
+    dl = torch.randn(out.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(20260523))
+    dtf = torch.empty(tuple(case["tf"].shape), device=dev)
+    dpar = torch.empty(5, device=dev)
+    dvol = torch.empty(case["volume"].shape, device=dev)
+    ts = []
+    for i in range(args.warmup + max(3, args.steps // 4)):
+        flush.zero_()
+        s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s0.record()
+        ctx.render(vid, cams, W, H, out=out)
+        s1.record()
+        ctx.render_backward(vid, cams, W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol)
+        s2.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append((s0.elapsed_time(s1), s1.elapsed_time(s2)))
+    ctx.free_volume(vid)
+    f_ms, b_ms = (float(np.mean([x[q] for x in ts])) for q in (0, 1))
+    return {"workload": "diff_head128_8cam: 128^3 float32 head, 8 cameras, 512x512, 1D TF 256",
+            "dense_samples": dense, "fwd_ms": f_ms, "bwd_ms": b_ms,
+            "fwd_gsamples_per_s": dense / (f_ms * 1e-3) / 1e9,
+            "fwd_bwd_gsamples_per_s": dense / ((f_ms + b_ms) * 1e-3) / 1e9}
+
+
 def run_batched(args, ctx, dev, flush):
     """Four uneven volumes x 64 orbit cameras at 512x512 in one persistent launch,
     replayed from a CUDA graph with the autotuned packet shape, beside the same 256
@@ -303,6 +350,17 @@ def run(args):
         dense_all = float(dense)
     value = dense_all / (ms * 1e-3) / 1e9
 
+    # Wall-clock frame rate of vr_render (launch included) on a warm context, device output.
+    walls = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        frame()
+        ctx.synchronize()
+        if i >= args.warmup:
+            walls.append(time.perf_counter() - t1)
+    fps_wall = 1.0 / float(np.mean(walls))
+
     # End to end through the C ABI with host buffers: uniforms + TF from host, image back to pinned host.
     tf_host = np.ascontiguousarray(case["tf"])
     e2e_times = []
@@ -367,8 +425,9 @@ def run(args):
                       "ms": float(np.median(pre[1:]))}
 
     batched = None if args.no_batch else run_batched(args, ctx, dev, flush)
+    multiview = None if args.no_backward else fwd_bwd_multiview(ctx, dev, flush, args)
     fit = None
-    if not args.no_fit and ws == 1:
+    if args.fit and ws == 1:
         from paper_2605_19737_gb300 import fit as fitmod
         fit = fitmod.run(steps=200)
     hbm, smax, peak_kind = _peaks()
@@ -380,7 +439,9 @@ def run(args):
     # whole brick store) plus the RGBA float32 image it writes
     frame_bytes = nbricks * BRICK_BYTES[kind] + W * H * 16
     sm_mhz = clk.get("sm_mhz") or smax
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp32_nominal = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fma_ms, fma_flops = ctx.fma_peak()
+    fp32_peak = fma_flops / 1e12
     achieved_tflops = evald * FLOPS_PER_SAMPLE[kind] / (ms * 1e-3) / 1e12
     if rank == 0:
         cb = None
@@ -395,14 +456,15 @@ def run(args):
                        "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows",
                        "step_vox": 0.5, "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "fps": 1000.0 / ms,
+            "fps": 1000.0 / ms, "fps_wall": fps_wall,
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                          "flops_per_evaluated_sample": FLOPS_PER_SAMPLE[kind],
                          "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (median SM clock under load)"
-                                        % sm_mhz},
+                         "peak_source": "measured: FP32 FMA probe vr_fma_peak (8 independent chains per thread, "
+                                        "%.3f ms per launch); nominal 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
+                                        % (fma_ms, sm_mhz, fp32_nominal)},
             "hbm_roofline": {"achieved": frame_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": frame_bytes / (ms * 1e-3) / 1e9 / hbm, "frac_vs_8tbs":
                              frame_bytes / (ms * 1e-3) / 1e9 / 8000.0, "bytes_per_frame": frame_bytes,
@@ -411,6 +473,7 @@ def run(args):
                     "d2h_bytes_per_step": int(W * H * 16), "ms_per_step": 1000.0 * e2e_s},
             "fwd_bwd": fwd_bwd,
             "batched": batched,
+            "fwd_bwd_multiview": multiview,
             "precompute": precompute,
             "fit": fit,
             "gpu_launches": args.steps,  # one raymarch kernel per timed frame
@@ -432,7 +495,7 @@ def main():
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--no-fit", action="store_true")
+    ap.add_argument("--fit", action="store_true", help="also run the 200-step transfer-function fit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

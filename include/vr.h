@@ -354,6 +354,17 @@ vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts,
  * after earlier work on the context's stream and before later work. */
 vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts* opts);
 
+/* Measure the device's FP32 FMA throughput (the paper has no counterpart; it is
+ * the roof the raymarch's arithmetic is reported against, since the raymarch is
+ * bound by the FP32 pipe and L1 rather than HBM). Launches, on the context's
+ * stream, `blocks` CTAs of 256 threads that each run 8 independent FMA chains for
+ * iters x 16 steps, `reps` times after one warm-up launch, timing each with CUDA
+ * events; synchronises. Writes the median launch time (ms) and the FLOPs of one
+ * launch (blocks * 256 * iters * 256). Allocates and frees a scratch output.
+ * Errors: INVALID_ARG (NULL pointers, blocks outside [1, 2^20], iters outside
+ * [1, 2^20], reps outside [1, 64]), OOM, CUDA. */
+vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms, double* h_flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -251,6 +251,16 @@ class Context:
         return dtf, dparams, (dvol if want_volume else None)
 
 
+    def fma_peak(self, blocks=None, iters=2048, reps=5):
+        """Measured FP32 FMA throughput: (median ms per launch, FLOP/s)."""
+        if blocks is None:
+            torch = _torch()
+            blocks = 8 * torch.cuda.get_device_properties(self.device).multi_processor_count
+        ms, flops = ctypes.c_float(), ctypes.c_double()
+        self._check(self._lib.vr_fma_peak(self._h, int(blocks), int(iters), int(reps), ctypes.byref(ms),
+                                          ctypes.byref(flops)))
+        return ms.value, flops.value / (ms.value * 1e-3)
+
     # -- batched rendering ----------------------------------------------------
     def batch_create(self, views):
         """views: iterable of (vol_id, camera (12,), out tensor (H, W, 4) on this device, W, H)."""

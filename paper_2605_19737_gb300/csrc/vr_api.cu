@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <string>
 #include <utility>
@@ -940,6 +941,40 @@ vr_status vr_batch_free(vr_ctx* ctx, int batch_id) {
     cudaFree(it->second->d_prefix);
     delete it->second;
     ctx->batches.erase(it);
+    return VR_OK;
+}
+
+vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms, double* h_flops) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!h_ms || !h_flops || blocks < 1 || blocks > (1 << 20) || iters < 1 || iters > (1 << 20) || reps < 1 ||
+        reps > 64)
+        return fail(ctx, VR_ERR_INVALID_ARG, "fma_peak: bad arguments");
+    DeviceGuard g(ctx->device);
+    float* out = nullptr;
+    CK(dalloc(&out, sizeof(float) * 256 * (size_t)blocks), "fma_peak scratch");
+    cudaEvent_t ev[2 * 64 + 2];
+    int made = 0;
+    cudaError_t e = cudaSuccess;
+    for (; made < 2 * reps && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+    if (e == cudaSuccess) e = launch_fma_peak(out, blocks, iters, ctx->stream);  // warm-up
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(ev[2 * r], ctx->stream);
+        if (e == cudaSuccess) e = launch_fma_peak(out, blocks, iters, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * r + 1], ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    std::vector<float> ms;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, ev[2 * r], ev[2 * r + 1]);
+        ms.push_back(t);
+    }
+    for (int q = 0; q < made; ++q) cudaEventDestroy(ev[q]);
+    cudaFree(out);
+    if (e != cudaSuccess) return fail(ctx, VR_ERR_CUDA, "fma_peak: %s", cudaGetErrorString(e));
+    std::sort(ms.begin(), ms.end());
+    *h_ms = ms[ms.size() / 2];
+    *h_flops = (double)blocks * 256.0 * (double)iters * 16.0 * 8.0 * 2.0;
     return VR_OK;
 }
 

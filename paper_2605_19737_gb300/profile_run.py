@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=8)
     ap.add_argument("--warps", type=int, default=4)
+    ap.add_argument("--backward", action="store_true", help="also run the adjoint raymarch after each frame")
     args = ap.parse_args()
     if args.workload == "head64":
         case = workloads.head64_128px()
@@ -44,16 +45,23 @@ def main():
         ctx.precompute_morphology(vid, case["sigmas"])
         ctx.set_tissue_params(vid, case["tf"], **case["params"])
         out = torch.empty((case["cams"].shape[0], case["H"], case["W"], 4), device="cuda")
-        ts = []
+        dl = torch.randn(out.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+        ts, tb = [], []
         for _ in range(args.frames):
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s, e, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             s.record()
             ctx.render(vid, case["cams"], case["W"], case["H"], out=out, kernel=kernel, packet_w=args.packet_w,
                        warps_per_block=args.warps)
             e.record()
+            if args.backward:
+                ctx.render_backward(vid, case["cams"], case["W"], case["H"], dl, kernel=kernel)
+            b.record()
             ctx.synchronize()
             ts.append(s.elapsed_time(e))
+            tb.append(e.elapsed_time(b))
     print("%s %s: %.3f ms/frame (mean of %d)" % (args.workload, args.kernel, float(np.mean(ts)), len(ts)))
+    if args.backward:
+        print("%s %s backward: %.3f ms/frame" % (args.workload, args.kernel, float(np.mean(tb))))
 
 
 if __name__ == "__main__":
