@@ -114,7 +114,8 @@ typedef enum {
 typedef struct {
     int kernel;         /* vr_kernel */
     int skip_empty;     /* 1: skip bricks classified empty (bit-neutral) */
-    int packet_w;       /* staged kernel: rays per packet along x (packet = 32 rays) */
+    int packet_w;       /* rays per warp packet along x (packet = 32 rays): 4, 8 or 16 for the
+                           per-lane kernels (default 4), also 32 for the staged and batched ones */
     int warps_per_block;/* staged kernel: warps per CTA, 1..16 */
 } vr_render_opts;
 
@@ -353,6 +354,16 @@ vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts,
  * (batch, packet shape, warps, skip) on a private stream and replays; ordered
  * after earlier work on the context's stream and before later work. */
 vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts* opts);
+
+/* Memory budget for the derived bricks (per-voxel I, gradient and Hessian, 12
+ * floats per corner voxel of each brick: about 5x the intensity bricks) that
+ * vr_precompute_morphology builds for the raymarch. A volume whose derived store
+ * would exceed `bytes` gets none -- its renders and gradients evaluate the
+ * per-sample stencils of the intensity bricks instead (same field up to
+ * rounding) -- and a later vr_precompute_morphology frees one it already has.
+ * Default 16 GiB; 0 disables derived bricks. Applies to subsequent
+ * vr_precompute_morphology calls of this context. Errors: INVALID_ARG (NULL ctx). */
+vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes);
 
 /* Measure the device's FP32 FMA throughput (the paper has no counterpart; it is
  * the roof the raymarch's arithmetic is reported against, since the raymarch is

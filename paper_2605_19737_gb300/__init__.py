@@ -212,7 +212,7 @@ class Context:
         return hist, pk
 
     # -- rendering ----------------------------------------------------------
-    def render(self, vol, cams, W, H, out=None, kernel=VR_KERNEL_AUTO, skip_empty=True, packet_w=8,
+    def render(self, vol, cams, W, H, out=None, kernel=VR_KERNEL_AUTO, skip_empty=True, packet_w=4,
                warps_per_block=4, counters=None, ray_samples=None):
         """Render (n, H, W, 4) premultiplied RGBA. ``out`` may be a device tensor or a
         pinned host tensor (then the library copies the image back on the stream)."""
@@ -229,7 +229,7 @@ class Context:
 
 
     def render_backward(self, vol, cams, W, H, dl_drgba, want_volume=True, skip_empty=True, dtf=None, dparams=None,
-                        dvol=None, kernel=VR_KERNEL_AUTO):
+                        dvol=None, kernel=VR_KERNEL_AUTO, packet_w=4):
         """Gradients of L given dL/dRGBA (device (n, H, W, 4)): returns (dtf (h, w, 4),
         dparams (5,) = gamma, ka, kd, ks, opacity_scale, dvolume (nz, ny, nx) or None)."""
         torch = _torch()
@@ -243,13 +243,18 @@ class Context:
         if want_volume and dvol is None:
             nx, ny, nz = self._keep[vol]
             dvol = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
-        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), 8, 4)
+        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), 4)
         g = dl_drgba.contiguous()
         self._check(self._lib.vr_render_backward(self._h, vol, carr, n, W, H, g.data_ptr(), dtf.data_ptr(),
                                                  dparams.data_ptr(), dvol.data_ptr() if want_volume else None,
                                                  ctypes.byref(opts)))
         return dtf, dparams, (dvol if want_volume else None)
 
+
+    def set_derived_budget(self, nbytes):
+        """Largest derived-brick store (bytes) later precompute_morphology calls build;
+        0 = none (per-sample stencils)."""
+        self._check(self._lib.vr_set_derived_budget(self._h, int(nbytes)))
 
     def fma_peak(self, blocks=None, iters=2048, reps=5):
         """Measured FP32 FMA throughput: (median ms per launch, FLOP/s)."""

@@ -49,6 +49,7 @@ struct Batch {
     ViewDev* d_views = nullptr;
     int* d_prefix = nullptr;        // 4 packet shapes x n_views
     int n_work[4] = {0, 0, 0, 0};   // packets per packet shape (packet_w = 4, 8, 16, 32)
+    bool all_derived = false;       // every view's volume has derived bricks
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (packet_w, warps) -> graph
 };
 
@@ -72,7 +73,8 @@ struct vr_ctx {
     size_t dgrad_cap = 0;
     unsigned* d_work = nullptr;   // [0]: staged-kernel work counter, [1]: status word
     int staged_ctas[2][17] = {};   // resident CTAs per SM by (vesselness, warps per block)
-    int batch_ctas[17] = {};       // resident batch-kernel CTAs per SM by warps per block
+    int batch_ctas[2][17] = {};    // resident batch-kernel CTAs per SM by (all derived, warps per block)
+    size_t derived_budget = kDerivedBudgetBytes;  // largest derived-brick store precompute builds
     std::map<int, Batch*> batches;
     int next_batch = 1;
     cudaStream_t graph_stream = nullptr;
@@ -373,7 +375,12 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
     // voxel-wise derivatives for the raymarch (Sec. 2.3), within a memory budget
     const size_t dbytes = sizeof(float) * (size_t)kDerBrickFloats * v->nbricks;
-    if (!v->d_dbricks && dbytes <= kDerivedBudgetBytes) {
+    if (v->d_dbricks && dbytes > ctx->derived_budget) {
+        CK(cudaStreamSynchronize(ctx->stream), "precompute_morphology: sync");
+        cudaFree(v->d_dbricks);
+        v->d_dbricks = nullptr;
+    }
+    if (!v->d_dbricks && dbytes <= ctx->derived_budget) {
         cudaError_t e = dalloc(&v->d_dbricks, dbytes);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -610,7 +617,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         return fail(ctx, VR_ERR_INVALID_ARG, "render: bad image size %d x %d x %d", n_cams, W, H);
     if (!v->morph_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_precompute_morphology first");
     if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_set_tissue_params first");
-    vr_render_opts o{VR_KERNEL_AUTO, 1, 8, 4};
+    vr_render_opts o{VR_KERNEL_AUTO, 1, 4, 4};
     if (opts) o = *opts;
     if (o.kernel < 0 || o.kernel > 3) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
     // VR_KERNEL_AUTO picks the per-lane gather kernel: on GB300 the bricked volume stays
@@ -621,6 +628,8 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8, 16 or 32");
     if (staged && (o.warps_per_block < 1 || o.warps_per_block > 8))
         return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be in [1, 8]");
+    if (!staged && o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8 or 16 for the per-lane kernels");
     DeviceGuard g(ctx->device);
     float* dst = out_rgba;
     const size_t img_bytes = sizeof(float) * 4 * (size_t)n_cams * W * H;
@@ -693,6 +702,10 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     fill_launch(B.r, v, W, H, skip);
     const bool staged = opts && opts->kernel == VR_KERNEL_STAGED;
     if (staged || (opts && opts->kernel == VR_KERNEL_GATHER_STENCIL)) B.r.vol.dbricks = nullptr;
+    B.r.packet_w = opts ? opts->packet_w : 4;
+    if (!staged && B.r.packet_w != 4 && B.r.packet_w != 8 && B.r.packet_w != 16)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: packet_w must be 4, 8 or 16");
+    B.r.packet_h = 32 / B.r.packet_w;
     // On the derived bricks, voxel gradients go first to per-voxel channel gradients
     // (vector atomics), then one gather pass applies the channels' stencil transposes.
     const bool channels = d_dvolume && B.r.vol.dbricks;
@@ -767,6 +780,7 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
         }
         b->n_work[si] = acc;
     }
+    bool all_derived = true;
     for (int i = 0; i < n; ++i) {
         const vr_view& vw = b->views[i];
         Volume* v = get_vol(ctx, vw.vol_id);
@@ -784,6 +798,14 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
         d.W = vw.W;
         d.H = vw.H;
         d.rc = L.rc;
+        all_derived = all_derived && L.vol.dbricks != nullptr;
+    }
+    if (all_derived != b->all_derived) {
+        // the captured graphs launch the other kernel variant
+        if (ctx->graph_stream) CK(cudaStreamSynchronize(ctx->graph_stream), "batch: graph sync");
+        for (auto& gx : b->graphs) cudaGraphExecDestroy(gx.second);
+        b->graphs.clear();
+        b->all_derived = all_derived;
     }
     CK(cudaMemcpyAsync(b->d_views, b->table.data(), sizeof(ViewDev) * n, cudaMemcpyHostToDevice, ctx->stream),
        "batch: upload views");
@@ -796,8 +818,8 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
 // Enqueue one batched launch on `st` (no host synchronisation, no allocation).
 vr_status batch_enqueue(vr_ctx* ctx, Batch* b, const vr_render_opts& o, vr_counters* ctr, cudaStream_t st) {
     const int si = shape_index(o.packet_w);
-    int& per_sm = ctx->batch_ctas[o.warps_per_block];
-    if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, &per_sm), "batch: occupancy");
+    int& per_sm = ctx->batch_ctas[b->all_derived][o.warps_per_block];
+    if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, b->all_derived, &per_sm), "batch: occupancy");
     if (per_sm < 1) return fail(ctx, VR_ERR_INVALID_ARG, "batch: kernel does not fit on an SM");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "batch: SM count");
@@ -817,7 +839,7 @@ vr_status batch_enqueue(vr_ctx* ctx, Batch* b, const vr_render_opts& o, vr_count
     if (ctas > need) ctas = need;
     if (ctas < 1) ctas = 1;
     CK(cudaMemsetAsync(ctx->d_work + 2, 0, sizeof(unsigned), st), "batch: reset work counter");
-    CK(launch_render_batch(B, o.warps_per_block, ctas, st), "batch kernel");
+    CK(launch_render_batch(B, o.warps_per_block, ctas, b->all_derived, st), "batch kernel");
     return VR_OK;
 }
 
@@ -904,8 +926,8 @@ vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts*
     auto git = b->graphs.find(key);
     if (git == b->graphs.end()) {
         // occupancy and SM count are queried outside the capture
-        int& per_sm = ctx->batch_ctas[o.warps_per_block];
-        if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, &per_sm), "batch: occupancy");
+        int& per_sm = ctx->batch_ctas[b->all_derived][o.warps_per_block];
+        if (per_sm == 0) CK(batch_ctas_per_sm(o.warps_per_block, b->all_derived, &per_sm), "batch: occupancy");
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
         vr_status es = batch_enqueue(ctx, b, o, nullptr, ctx->graph_stream);
@@ -975,6 +997,12 @@ vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms,
     std::sort(ms.begin(), ms.end());
     *h_ms = ms[ms.size() / 2];
     *h_flops = (double)blocks * 256.0 * (double)iters * 16.0 * 8.0 * 2.0;
+    return VR_OK;
+}
+
+vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    ctx->derived_budget = (size_t)bytes;
     return VR_OK;
 }
 

@@ -169,8 +169,10 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
     float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
     TfGradSink sink(tf_dst, B.tf_in_smem != 0, L.tp.tf_w, L.tp.tf_h > 1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int i = blockIdx.x * 16 + (w & 1) * 8 + (l & 7);
-    const int j = blockIdx.y * 8 + (w >> 1) * 4 + (l >> 3);
+    int di, dj;
+    tile_pixel(L.packet_w, w, l, di, dj);
+    const int i = blockIdx.x * 16 + di;
+    const int j = blockIdx.y * 8 + dj;
     const int cam = blockIdx.z;
     const bool inside = i < L.W && j < L.H;
     const VolumeDev& v = L.vol;

@@ -28,7 +28,7 @@ constexpr int kMaxCamsPerLaunch = 64;
 constexpr int kDerEdge = 9;
 constexpr int kDerFloats = 12;
 constexpr int kDerBrickFloats = kDerEdge * kDerEdge * kDerEdge * kDerFloats;  // 8748 floats = 34,992 B
-constexpr size_t kDerivedBudgetBytes = (size_t)16 << 30;  // built only below this size
+constexpr size_t kDerivedBudgetBytes = (size_t)16 << 30;  // default: built only up to this size
 
 struct CamDev {
     float eye[3], fwd[3], right[3], up[3];
@@ -86,12 +86,22 @@ struct RenderLaunch {
     unsigned* ray_samples;     // nullable, [n_cams][H][W][2]
     int W, H, n_cams, cam_offset;
     int skip;
-    int packet_w, packet_h;    // staged kernel packet shape (packet_w * packet_h == 32)
+    int packet_w, packet_h;    // ray packet of a warp (packet_w * packet_h == 32); per-lane kernels: 4, 8 or 16 wide
     unsigned* work_counter;    // staged kernel work queue (zeroed before launch)
     unsigned* status;          // device status word (kStatusTimeout on an expired wait)
     int n_packets_x, n_packets_y, n_work;
     CamDev cams[kMaxCamsPerLaunch];
 };
+
+// Pixel offset (di, dj) of lane l of warp w within a per-lane kernel's 16 x 8 CTA
+// tile, for warp packets of packet_w x (32 / packet_w) rays, packet_w in {4, 8, 16}.
+__device__ __forceinline__ void tile_pixel(int packet_w, int w, int l, int& di, int& dj) {
+    const int pl = __ffs(packet_w) - 1;  // log2 packet_w
+    const int wl = 4 - pl;               // log2 of the warps across the tile
+    const int wx = w & ((1 << wl) - 1), wy = w >> wl;
+    di = (wx << pl) + (l & (packet_w - 1));
+    dj = wy * (32 >> pl) + (l >> pl);
+}
 
 struct BackwardLaunch {
     RenderLaunch r;
@@ -170,8 +180,9 @@ cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, fl
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t st);
 cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
                                       cudaStream_t st);
-cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, cudaStream_t st);
-cudaError_t batch_ctas_per_sm(int warps_per_block, int* per_sm);
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,
+                                cudaStream_t st);
+cudaError_t batch_ctas_per_sm(int warps_per_block, bool all_derived, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
 int staged_smem_bytes(int warps_per_block, bool vessel);
 // Set the kernel's dynamic shared-memory limit and report resident CTAs per SM.

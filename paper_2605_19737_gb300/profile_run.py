@@ -26,7 +26,7 @@ def main():
     ap.add_argument("--workload", default="brainweb_1080p", choices=["brainweb_1080p", "brainweb_540p", "head64"])
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--frames", type=int, default=3)
-    ap.add_argument("--packet-w", type=int, default=8)
+    ap.add_argument("--packet-w", type=int, default=4)
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--backward", action="store_true", help="also run the adjoint raymarch after each frame")
     args = ap.parse_args()

@@ -26,17 +26,20 @@ def vr(torch):
     ctx.close()
 
 
-def _volumes(vr, torch):
-    """Three uneven volumes with different transfer functions (1D, 2D gradient, vessel)."""
+def _volumes(vr, torch, stencil_only=()):
+    """Three uneven volumes with different transfer functions (1D, 2D gradient, vessel);
+    those whose index is in stencil_only get no derived bricks (per-sample stencils)."""
     out = []
     a = workloads.head64_128px()
     b = workloads.scaled_brainweb((45, 53, 41))
     c = workloads.vessel_1080p(dims=(40, 36, 30), width=8, height=8)
-    for case in (a, b, c):
+    for n, case in enumerate((a, b, c)):
         vol = case["volume"]
         vid = vr.load_volume(torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda(),
                              case["spacing"])
+        vr.set_derived_budget(0 if n in stencil_only else 16 << 30)
         vr.precompute_morphology(vid, case["sigmas"])
+        vr.set_derived_budget(16 << 30)
         vr.set_tissue_params(vid, case["tf"], **case["params"])
         dims = vol.shape[::-1]
         out.append((vid, dims))
@@ -54,10 +57,13 @@ def _views(torch, vols, n_per=5):
     return views
 
 
-@pytest.mark.parametrize("packet_w,warps", [(8, 8), (4, 2), (32, 4), (16, 1)])
-def test_batch_equals_single_views(vr, torch, packet_w, warps):
+@pytest.mark.parametrize("packet_w,warps,stencil_only", [(8, 8, ()), (4, 2, ()), (32, 4, ()), (16, 1, ()),
+                                                        (4, 4, (1,)), (8, 8, (0, 2))])
+def test_batch_equals_single_views(vr, torch, packet_w, warps, stencil_only):
+    """Bit for bit equal to vr_render of each view, also for batches that mix volumes
+    with and without derived bricks (the batch then takes each view's path at run time)."""
     import paper_2605_19737_gb300 as pkg
-    vols = _volumes(vr, torch)
+    vols = _volumes(vr, torch, stencil_only)
     views = _views(torch, vols)
     bid = vr.batch_create(views)
     ctr = pkg.new_counters()

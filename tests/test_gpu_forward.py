@@ -186,6 +186,50 @@ def test_staged_equals_gather_bitwise(vr, torch, packet_w, warps):
     vr.free_volume(vid)
 
 
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_packet_shape_only_moves_pixels(vr, torch, kernel):
+    """The warp packet shape of the per-lane kernels assigns rays to lanes and nothing
+    else: 4x8, 8x4 and 16x2 packets give bit-identical images and counts (ragged
+    100x75 tiles), and the backward's gradients agree to rounding of atomics; a
+    packet 32 wide does not fit the 16-wide tile and is refused."""
+    case = workloads.scaled_brainweb((61, 73, 59), width=100, height=75, n_cams=2)
+    vid = _load_case(vr, torch, case)
+    ref, rref = _render(vr, torch, vid, case, kernel=kernel, packet_w=4)
+    for pw in (8, 16):
+        a, ra = _render(vr, torch, vid, case, kernel=kernel, packet_w=pw)
+        np.testing.assert_array_equal(a, ref)
+        np.testing.assert_array_equal(ra, rref)
+    g = torch.from_numpy(np.random.default_rng(5).normal(size=ref.shape).astype(np.float32)).cuda()
+    d4 = [x.cpu().numpy() for x in vr.render_backward(vid, case["cams"], 100, 75, g, kernel=kernel, packet_w=4)]
+    d16 = [x.cpu().numpy() for x in vr.render_backward(vid, case["cams"], 100, 75, g, kernel=kernel, packet_w=16)]
+    for x, y in zip(d4, d16):
+        assert np.linalg.norm(x - y) <= 1e-5 * max(np.linalg.norm(x), 1e-30)
+    import paper_2605_19737_gb300 as pkg
+    with pytest.raises(pkg.VRError):
+        vr.render(vid, case["cams"], 100, 75, kernel=kernel, packet_w=32)
+    vr.free_volume(vid)
+
+
+def test_derived_budget_selects_the_stencil_path(vr, torch):
+    """With a derived-brick budget below the volume's store the default kernel
+    evaluates the per-sample stencils: equal bit for bit to VR_KERNEL_GATHER_STENCIL;
+    raising the budget and re-running the precompute brings the derived path back."""
+    case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
+    vid = _load_case(vr, torch, case)
+    derived, _ = _render(vr, torch, vid, case, kernel=1)
+    stencil, rs = _render(vr, torch, vid, case, kernel=3)
+    vr.set_derived_budget(1 << 20)  # smaller than this volume's ~14 MB derived store
+    vr.precompute_morphology(vid, case["sigmas"])
+    a, ra = _render(vr, torch, vid, case, kernel=1)
+    np.testing.assert_array_equal(a, stencil)
+    np.testing.assert_array_equal(ra, rs)
+    vr.set_derived_budget(16 << 30)
+    vr.precompute_morphology(vid, case["sigmas"])
+    b, _ = _render(vr, torch, vid, case, kernel=1)
+    np.testing.assert_array_equal(b, derived)
+    vr.free_volume(vid)
+
+
 def test_zero_opacity_and_host_output(vr, torch):
     case = workloads.head64_128px()
     vid = _load_case(vr, torch, case)
