@@ -191,14 +191,15 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
     dtf = torch.empty(tuple(case["tf"].shape), device=dev)
     dpar = torch.empty(5, device=dev)
     dvol = torch.empty(case["volume"].shape, device=dev)
+    state = torch.empty((cams.shape[0], H, W, 2), device=dev)
     ts = []
     for i in range(args.warmup + max(3, args.steps // 4)):
         flush.zero_()
         s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         s0.record()
-        ctx.render(vid, cams, W, H, out=out)
+        ctx.render(vid, cams, W, H, out=out, ray_state=state)
         s1.record()
-        ctx.render_backward(vid, cams, W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol)
+        ctx.render_backward(vid, cams, W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol, ray_state=state)
         s2.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -388,22 +389,28 @@ def run(args):
         dtf = torch.empty(tuple(case["tf"].shape), device=dev)
         dpar = torch.empty(5, device=dev)
         dvol = torch.empty(vol_np.shape, device=dev)
+        state = torch.empty((1, H, W, 2), device=dev)
         fb = []
         for i in range(args.warmup + max(3, args.steps // 4)):
             flush.zero_()
-            s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            s0, s1, s2, s3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             s0.record()
-            frame()
+            ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, ray_state=state)
             s1.record()
-            ctx.render_backward(vid, case["cams"], W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol)
+            ctx.render_backward(vid, case["cams"], W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol, ray_state=state)
             s2.record()
+            ctx.render_backward(vid, case["cams"], W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol)
+            s3.record()
             torch.cuda.synchronize()
             if i >= args.warmup:
-                fb.append((s0.elapsed_time(s1), s1.elapsed_time(s2)))
-        f_ms, b_ms = (float(np.mean([x[q] for x in fb])) for q in (0, 1))
+                fb.append((s0.elapsed_time(s1), s1.elapsed_time(s2), s2.elapsed_time(s3)))
+        f_ms, b_ms, r_ms = (float(np.mean([x[q] for x in fb])) for q in (0, 1, 2))
         fwd_bwd = {"gsamples_per_s": dense_all / ((f_ms + b_ms) * 1e-3) / 1e9, "ms_per_step": f_ms + b_ms,
                    "fwd_ms": f_ms, "bwd_ms": b_ms, "fps": 1000.0 / (f_ms + b_ms),
+                   "bwd_ms_re_march": r_ms,
                    "grads": "transfer function 256x64x4, 5 uniforms, 181x217x181 voxels",
+                   "note": "forward records per-ray state (last sample, transmittance), the backward starts "
+                           "its reverse sweeps there; bwd_ms_re_march: the backward re-marching each ray instead",
                    "plain_fwd_gsamples_per_s": value}
 
     # Per-volume vesselness precompute (sigma 1, 2, 3) on the 256x256x176 vessel phantom.

@@ -117,6 +117,12 @@ typedef struct {
     int packet_w;       /* rays per warp packet along x (packet = 32 rays): 4, 8 or 16 for the
                            per-lane kernels (default 4), also 32 for the staged and batched ones */
     int warps_per_block;/* staged kernel: warps per CTA, 1..16 */
+    void* ray_state;    /* NULL, or device memory of n_cams*H*W x 8 bytes (per-lane kernels
+                           only): vr_render writes, per pixel, the index of the ray's last
+                           sample (int32; -1 for none) and the transmittance in front of it
+                           (float32); vr_render_backward with the same volume, tissue
+                           parameters, cameras and size reads it instead of re-marching each
+                           ray forward. Zero it when constructing the struct. */
 } vr_render_opts;
 
 /* ------------------------------------------------------------------ context */
@@ -260,7 +266,8 @@ vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long
  *   d_counters: NULL or device vr_counters to add into.
  *   d_ray_samples: NULL or device uint32 [n_cams][H][W][2] receiving each
  *             ray's dense and evaluated sample counts.
- * Errors: INVALID_ARG (n_cams < 1, W or H outside [1, 16384]), NOT_READY
+ * Errors: INVALID_ARG (n_cams < 1, W or H outside [1, 16384], a ray_state with
+ * the staged kernel), NOT_READY
  * (no vr_precompute_morphology or vr_set_tissue_params yet), OOM, CUDA. */
 vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
                     int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
@@ -282,7 +289,9 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * reverse sweep visits every sample, empty bricks included: a zero-opacity
  * sample still gives the opacity entries it reads a gradient.
  * opts: NULL or as vr_render: skip_empty applies to the forward re-march only,
- * where it is exact; kernel VR_KERNEL_STAGED sweeps brick by brick and sums voxel
+ * where it is exact; a non-NULL ray_state (written by the vr_render of this image)
+ * replaces the re-march: each ray's reverse sweep starts from its recorded last
+ * sample and transmittance (per-lane kernels only); kernel VR_KERNEL_STAGED sweeps brick by brick and sums voxel
  * gradients in shared memory before global atomics (per-sample stencils), any
  * other value (default) sweeps each lane independently and adds voxel gradients
  * with global atomics, evaluating samples from the derived bricks when they exist

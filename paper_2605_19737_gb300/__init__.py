@@ -29,6 +29,15 @@ def _torch():
     return torch
 
 
+def _state_ptr(state, n, W, H):
+    """Device pointer of a per-ray state tensor (n*H*W*8 bytes), or None."""
+    if state is None:
+        return None
+    if not (state.is_cuda and state.is_contiguous() and state.numel() * state.element_size() == 8 * n * W * H):
+        raise ValueError("ray_state must be a contiguous device tensor of n*H*W*8 bytes")
+    return state.data_ptr()
+
+
 def _stream_handle(stream):
     if stream is None:
         torch = _torch()
@@ -213,14 +222,17 @@ class Context:
 
     # -- rendering ----------------------------------------------------------
     def render(self, vol, cams, W, H, out=None, kernel=VR_KERNEL_AUTO, skip_empty=True, packet_w=4,
-               warps_per_block=4, counters=None, ray_samples=None):
+               warps_per_block=4, counters=None, ray_samples=None, ray_state=None):
         """Render (n, H, W, 4) premultiplied RGBA. ``out`` may be a device tensor or a
-        pinned host tensor (then the library copies the image back on the stream)."""
+        pinned host tensor (then the library copies the image back on the stream).
+        ``ray_state``: optional device tensor of n*H*W*8 bytes (e.g. (n, H, W, 2) float32)
+        that receives each ray's last sample and transmittance for render_backward."""
         torch = _torch()
         carr, n = cameras_to_c(cams)
         if out is None:
             out = torch.empty((n, H, W, 4), dtype=torch.float32, device="cuda:%d" % self.device)
-        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), int(warps_per_block))
+        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), int(warps_per_block),
+                              _state_ptr(ray_state, n, W, H))
         p, dev = _ptr(out)
         self._check(self._lib.vr_render(self._h, vol, carr, n, W, H, p, int(not dev), ctypes.byref(opts),
                                         counters.data_ptr() if counters is not None else None,
@@ -229,7 +241,7 @@ class Context:
 
 
     def render_backward(self, vol, cams, W, H, dl_drgba, want_volume=True, skip_empty=True, dtf=None, dparams=None,
-                        dvol=None, kernel=VR_KERNEL_AUTO, packet_w=4):
+                        dvol=None, kernel=VR_KERNEL_AUTO, packet_w=4, ray_state=None):
         """Gradients of L given dL/dRGBA (device (n, H, W, 4)): returns (dtf (h, w, 4),
         dparams (5,) = gamma, ka, kd, ks, opacity_scale, dvolume (nz, ny, nx) or None)."""
         torch = _torch()
@@ -243,7 +255,7 @@ class Context:
         if want_volume and dvol is None:
             nx, ny, nz = self._keep[vol]
             dvol = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
-        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), 4)
+        opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), 4, _state_ptr(ray_state, n, W, H))
         g = dl_drgba.contiguous()
         self._check(self._lib.vr_render_backward(self._h, vol, carr, n, W, H, g.data_ptr(), dtf.data_ptr(),
                                                  dparams.data_ptr(), dvol.data_ptr() if want_volume else None,

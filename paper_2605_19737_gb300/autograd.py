@@ -9,9 +9,13 @@
                     before rendering, and its gradient is returned.
 The other uniforms (tf_mode, grad_mod, shading, kappa_ref, w_max, et_threshold,
 step_vox) are passed as a dict and held fixed. Both passes run in libvr.so's
-CUDA kernels; this module only moves tensors across the C ABI.
+CUDA kernels; this module only moves tensors across the C ABI. When a gradient
+is wanted, the forward also records each ray's last sample and transmittance
+(8 bytes per pixel), so that the backward starts its reverse sweeps from them
+instead of re-marching every ray.
 """
 
+import numpy as np
 import torch
 
 PARAM_NAMES = ("gamma", "ka", "kd", "ks", "opacity_scale")
@@ -26,7 +30,11 @@ class RenderFunction(torch.autograd.Function):
             vr_ctx.set_normalized(vol, norm_volume.detach().contiguous())
         tfc = tf.detach().contiguous()
         vr_ctx.set_tissue_params(vol, tfc, **uniforms)
-        img = vr_ctx.render(vol, cams, W, H)
+        n = np.asarray(cams, dtype=np.float32).reshape(-1, 12).shape[0]
+        state = (torch.empty((n, H, W, 2), dtype=torch.float32, device=tfc.device)
+                 if any(fctx.needs_input_grad[:3]) else None)
+        img = vr_ctx.render(vol, cams, W, H, ray_state=state)
+        fctx.state = state
         fctx.vr = (vr_ctx, vol, cams, W, H, uniforms)
         fctx.save_for_backward(tfc)
         fctx.has_vol = norm_volume is not None
@@ -39,7 +47,8 @@ class RenderFunction(torch.autograd.Function):
         (tfc,) = fctx.saved_tensors
         vr_ctx.set_tissue_params(vol, tfc, **uniforms)  # the state the image was made with
         want_vol = fctx.has_vol and fctx.needs_input_grad[2]
-        dtf, dpar, dvol = vr_ctx.render_backward(vol, cams, W, H, grad_img.contiguous(), want_volume=want_vol)
+        dtf, dpar, dvol = vr_ctx.render_backward(vol, cams, W, H, grad_img.contiguous(), want_volume=want_vol,
+                                                 ray_state=fctx.state)
         return (dtf if fctx.needs_input_grad[0] else None,
                 dpar.to(fctx.params_device) if fctx.needs_input_grad[1] else None,
                 dvol, None, None, None, None, None, None)

@@ -617,9 +617,11 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         return fail(ctx, VR_ERR_INVALID_ARG, "render: bad image size %d x %d x %d", n_cams, W, H);
     if (!v->morph_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_precompute_morphology first");
     if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_set_tissue_params first");
-    vr_render_opts o{VR_KERNEL_AUTO, 1, 4, 4};
+    vr_render_opts o{VR_KERNEL_AUTO, 1, 4, 4, nullptr};
     if (opts) o = *opts;
     if (o.kernel < 0 || o.kernel > 3) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
+    if (o.kernel == VR_KERNEL_STAGED && o.ray_state)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: ray_state needs a per-lane kernel");
     // VR_KERNEL_AUTO picks the per-lane gather kernel: on GB300 the bricked volume stays
     // L1/L2-resident and per-lane marching keeps 91% of lanes busy, while staging one
     // brick per warp idles the lanes outside it (ncu: 58% SIMT efficiency).
@@ -642,6 +644,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.out = dst;
     L.counters = d_counters;
     L.ray_samples = d_ray_samples;
+    L.ray_state = static_cast<float2*>(o.ray_state);
     if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr;
     L.packet_w = o.packet_w;
     L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
@@ -703,6 +706,9 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     const bool staged = opts && opts->kernel == VR_KERNEL_STAGED;
     if (staged || (opts && opts->kernel == VR_KERNEL_GATHER_STENCIL)) B.r.vol.dbricks = nullptr;
     B.r.packet_w = opts ? opts->packet_w : 4;
+    B.r.ray_state = opts ? static_cast<float2*>(opts->ray_state) : nullptr;
+    if (staged && B.r.ray_state)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: ray_state needs a per-lane kernel");
     if (!staged && B.r.packet_w != 4 && B.r.packet_w != 8 && B.r.packet_w != 16)
         return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: packet_w must be 4, 8 or 16");
     B.r.packet_h = 32 / B.r.packet_w;
@@ -844,7 +850,7 @@ vr_status batch_enqueue(vr_ctx* ctx, Batch* b, const vr_render_opts& o, vr_count
 }
 
 vr_status batch_opts(vr_ctx* ctx, const vr_render_opts* opts, vr_render_opts* o) {
-    *o = vr_render_opts{VR_KERNEL_AUTO, 1, 8, 8};
+    *o = vr_render_opts{VR_KERNEL_AUTO, 1, 8, 8, nullptr};
     if (opts) *o = *opts;
     if (shape_index(o->packet_w) < 0) return fail(ctx, VR_ERR_INVALID_ARG, "batch: packet_w must be 4, 8, 16 or 32");
     if (o->warps_per_block < 1 || o->warps_per_block > 8)

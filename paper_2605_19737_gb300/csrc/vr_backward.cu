@@ -189,42 +189,53 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
     if (hit) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         const float4 g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
-        // 1. forward re-march
-        float A = 0.f, A_prev = 0.f;
-        int k = 0, kstop = r.ns - 1, klast = -1;
-        while (k < r.ns) {
-            const float kk = (float)k + 0.5f;
-            int i0[3], bc[3];
-            float f[3];
+        // 1. the ray's last sample and the transmittance in front of it: recorded by the
+        // forward render (ray_state), or re-marched forward here
+        int kstop = r.ns - 1;
+        float Tk;
+        if (L.ray_state) {
+            const float2 st = __ldg(L.ray_state + pix);
+            kstop = __float_as_int(st.x);
+            Tk = st.y;
+        } else {
+            float A = 0.f, A_prev = 0.f;
+            int k = 0, klast = -1;
+            while (k < r.ns) {
+                const float kk = (float)k + 0.5f;
+                int i0[3], bc[3];
+                float f[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
-                bc[q] = i0[q] >> 3;
+                for (int q = 0; q < 3; ++q) {
+                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    bc[q] = i0[q] >> 3;
+                }
+                const long long bi = bidx(v, bc);
+                if (L.skip && __ldg(v.empty + bi)) {
+                    k = brick_exit_k(r, bc, k, r.ns);
+                    continue;
+                }
+                const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
+                                 (i0[0] - kCells * bc[0]);
+                float fld[10];
+                eval_field<kDerived>(v, bi, i0, bc, base, f, is, fld);
+                const float vval =
+                    v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+                float alpha, col[3];
+                sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                const float wgt = (1.0f - A) * alpha;  // as the forward kernel composites
+                A_prev = A;
+                A += wgt;
+                klast = k;
+                if (A >= et) {
+                    kstop = k;
+                    break;
+                }
+                ++k;
             }
-            const long long bi = bidx(v, bc);
-            if (L.skip && __ldg(v.empty + bi)) {
-                k = brick_exit_k(r, bc, k, r.ns);
-                continue;
-            }
-            const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
-                             (i0[0] - kCells * bc[0]);
-            float fld[10];
-            eval_field<kDerived>(v, bi, i0, bc, base, f, is, fld);
-            const float vval = v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
-            float alpha, col[3];
-            sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
-            A_prev = A;
-            A += (1.0f - A) * alpha;
-            klast = k;
-            if (A >= et) {
-                kstop = k;
-                break;
-            }
-            ++k;
+            // transmittance before the stopping sample (1 when no sample had opacity)
+            Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
         }
         {
-            // transmittance before the stopping sample (1 when no sample had opacity)
-            float Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
             float Tk1 = Tk, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;
             const float dC[3] = {g4.x, g4.y, g4.z};
             // 2. reverse sweep

@@ -84,6 +84,7 @@ struct RenderLaunch {
     float* out;                // [n_cams][H][W][4]
     vr_counters* counters;     // nullable
     unsigned* ray_samples;     // nullable, [n_cams][H][W][2]
+    float2* ray_state;         // nullable, [n_cams][H][W]: (last sample index as int bits, transmittance before it)
     int W, H, n_cams, cam_offset;
     int skip;
     int packet_w, packet_h;    // ray packet of a warp (packet_w * packet_h == 32); per-lane kernels: 4, 8 or 16 wide

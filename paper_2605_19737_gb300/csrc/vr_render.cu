@@ -42,11 +42,18 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
 
 // Front-to-back march of one ray (Eqs. 4-6) over the bricked volume in HBM/L2,
 // skipping bricks classified empty. Shared by the single-view and batched kernels.
-template <bool kDerived>
+// With kState it also returns the ray's last sample index (kstop) and the
+// transmittance in front of that sample (t_last), which the adjoint sweep starts from.
+template <bool kDerived, bool kState = false>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
-                                             float4& out, unsigned& dense, unsigned& evald) {
+                                             float4& out, unsigned& dense, unsigned& evald, int* klast_out = nullptr,
+                                             float* t_last = nullptr) {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    float A_prev = 0.f;  // kState: A before the last evaluated sample
+    int klast = -1;      // kState: last evaluated sample
+    int k1 = -1;         // kState: first sample with A >= 1 (where the adjoint sweep must start
+    float T1 = 1.f;      // when early termination is off) and the transmittance in front of it
     int k = 0, kstop = -1;
     unsigned ne = 0;
     // The skip flag and the base pointers of the current brick are re-read only
@@ -96,7 +103,15 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         C0 = fmaf(col[0], wgt, C0);
         C1 = fmaf(col[1], wgt, C1);
         C2 = fmaf(col[2], wgt, C2);
+        if (kState) {
+            A_prev = A;
+            klast = k;
+        }
         A += wgt;
+        if (kState && k1 < 0 && A >= 1.0f) {
+            k1 = k;
+            T1 = 1.0f - A_prev;
+        }
         ++ne;
         if (A >= tp.et_threshold) {
             kstop = k;
@@ -107,10 +122,17 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     out = make_float4(C0, C1, C2, A);
     dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;
     evald = ne;
+    if (kState) {
+        // the adjoint sweep starts at the first sample with A >= min(et, 1): the stopping
+        // sample, or (early termination off) the first that made A reach 1
+        const int kl = (int)dense - 1;
+        *klast_out = k1 >= 0 ? k1 : kl;
+        *t_last = k1 >= 0 ? T1 : ((klast == kl) ? 1.0f - A_prev : 1.0f - A);  // samples after klast: alpha 0
+    }
 }
 
 // 7 resident CTAs per SM for the derived-brick path (<= 73 registers), 6 for the stencils.
-template <bool kDerived>
+template <bool kDerived, bool kState>
 __global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
@@ -129,10 +151,13 @@ __global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const _
     const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned dense = 0, evald = 0;
-    if (hit) march_gather<kDerived>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald);
+    int kl = -1;
+    float tl = 1.0f;
+    if (hit) march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, &kl, &tl);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         reinterpret_cast<float4*>(L.out)[pix] = px;
+        if (kState) L.ray_state[pix] = make_float2(__int_as_float(kl), tl);
         if (L.ray_samples) {
             L.ray_samples[2 * pix] = dense;
             L.ray_samples[2 * pix + 1] = evald;
@@ -203,10 +228,18 @@ __global__ void __launch_bounds__(256, 3) k_render_batch_mixed(const __grid_cons
 
 cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st) {
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
-    if (L.vol.dbricks)
-        k_render_gather<true><<<grid, 128, 0, st>>>(L);
-    else
-        k_render_gather<false><<<grid, 128, 0, st>>>(L);
+    const bool state = L.ray_state != nullptr;
+    if (L.vol.dbricks) {
+        if (state)
+            k_render_gather<true, true><<<grid, 128, 0, st>>>(L);
+        else
+            k_render_gather<true, false><<<grid, 128, 0, st>>>(L);
+    } else {
+        if (state)
+            k_render_gather<false, true><<<grid, 128, 0, st>>>(L);
+        else
+            k_render_gather<false, false><<<grid, 128, 0, st>>>(L);
+    }
     return cudaGetLastError();
 }
 

@@ -47,7 +47,7 @@ class vr_view(ctypes.Structure):
 
 class vr_render_opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("skip_empty", ctypes.c_int), ("packet_w", ctypes.c_int),
-                ("warps_per_block", ctypes.c_int)]
+                ("warps_per_block", ctypes.c_int), ("ray_state", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p

@@ -64,7 +64,8 @@ def _cases():
     return {"head_1d": small, "brainweb_2d": bw, "head_1d_corrected": corr}
 
 
-@pytest.mark.parametrize("kernel", [0, 2, 3])  # per-lane (derived bricks), brick-synchronous, per-lane stencils
+@pytest.mark.parametrize("kernel", [0, 2, 3, "state"])  # per-lane (derived bricks), brick-synchronous,
+#                                                          per-lane stencils, per-lane from the forward's ray state
 @pytest.mark.parametrize("name", ["head_1d", "brainweb_2d", "head_1d_corrected"])
 def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     case = _cases()[name]
@@ -82,8 +83,13 @@ def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     dl[amb] = 0.0
     dtf_o, dpar_o, dvol_o = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H, dl,
                                                gmax_value=gmax)
+    state = None
+    if kernel == "state":
+        state = torch.empty((n, H, W, 2), dtype=torch.float32, device="cuda")
+        vr.render(vid, case["cams"], W, H, ray_state=state)
+        kernel = 0
     dtf, dpar, dvol = vr.render_backward(vid, case["cams"], W, H, torch.from_numpy(dl.astype(np.float32)).cuda(),
-                                         kernel=kernel)
+                                         kernel=kernel, ray_state=state)
     dtf, dpar, dvol = dtf.cpu().numpy(), dpar.cpu().numpy(), dvol.cpu().numpy()
     e_tf, e_vol = _rel(dtf, dtf_o), _rel(dvol, dvol_o)
     used = [0, 1, 2, 3, 4] if case["params"]["shading"] else [0, 4]
@@ -91,6 +97,43 @@ def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     print("%s: rel err tf %.2e params %.2e volume %.2e (ambiguous rays %d)" % (name, e_tf, e_par, e_vol, amb.sum()))
     assert np.linalg.norm(dtf_o) > 0 and np.linalg.norm(dvol_o) > 0
     assert e_tf <= TOL_GRAD and e_par <= TOL_GRAD and e_vol <= TOL_GRAD
+    vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("variant", ["et", "no_et", "opaque_no_et"])
+def test_ray_state_replaces_the_re_march(vr, torch, variant):
+    """The per-ray state the forward records (last sample, transmittance in front of
+    it) gives the backward the re-march's starting point: equal gradients; with early
+    termination the recorded index is the dense sample count - 1; with it off and
+    fully opaque samples (A reaches 1) the sweep starts at the first of them."""
+    case = _cases()["head_1d"]
+    if variant != "et":
+        case["params"] = dict(case["params"], et_threshold=2.0)
+    if variant == "opaque_no_et":
+        case["params"] = dict(case["params"], opacity_scale=60.0)
+    In32 = oracle.normalize(case["volume"]).astype(np.float32)
+    vid = _setup(vr, torch, case, In32)
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+    state = torch.empty((n, H, W, 2), dtype=torch.float32, device="cuda")
+    rs = torch.zeros((n, H, W, 2), dtype=torch.int32, device="cuda")
+    img = vr.render(vid, case["cams"], W, H, ray_state=state, ray_samples=rs)
+    torch.cuda.synchronize()
+    kl = state[..., 0].contiguous().view(torch.int32).cpu().numpy()
+    dense = rs[..., 0].cpu().numpy()
+    if variant != "opaque_no_et":
+        np.testing.assert_array_equal(kl, dense - 1)
+    else:
+        assert (kl < dense - 1).sum() > 0 and np.all(kl <= dense - 1)
+        assert float(img[..., 3].max()) == 1.0
+    t = state[..., 1].cpu().numpy()
+    assert np.all((t >= 0.0) & (t <= 1.0))
+    dl = torch.from_numpy(np.random.default_rng(75).normal(size=(n, H, W, 4)).astype(np.float32)).cuda()
+    a = [x.cpu().numpy() for x in vr.render_backward(vid, case["cams"], W, H, dl)]
+    b = [x.cpu().numpy() for x in vr.render_backward(vid, case["cams"], W, H, dl, ray_state=state)]
+    for x, y in zip(a, b):
+        # the two starting points differ only by the rounding of A (float32 contraction)
+        assert np.all(np.isfinite(y))
+        assert _rel(y, x) <= 1e-4
     vr.free_volume(vid)
 
 
