@@ -76,59 +76,20 @@ struct TfGradSink {
     }
 };
 
-// dfield receives dL/d(I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz) in the same
-// (spacing-scaled) units as the sample field f.
-__device__ __forceinline__ void sample_adjoint(const float f[10], float vval, const float dir[3], const TissueDev& tp,
-                                               const float4* __restrict__ tf, float inv_gmax, float da,
-                                               const float dc[3], TfGradSink& dtf, ParamGrad& dp,
-                                               float dfield[10]) {
+// Adjoint of one sample's optics, from the forward values `o` that optics_core
+// computed for it. da = dL/dalpha and dc = dL/dcolour come in; the transfer-function
+// and uniform gradients go to dtf and dp; dfield receives dL/d(I, gx, gy, gz, Hxx,
+// Hyy, Hzz, Hxy, Hxz, Hyz) in the same (spacing-scaled) units as the field f.
+__device__ __forceinline__ void sample_adjoint(const float f[10], const SampleOptics& o, const float dir[3],
+                                               const TissueDev& tp, float inv_gmax, float da, const float dc[3],
+                                               TfGradSink& dtf, ParamGrad& dp, float dfield[10]) {
     const float gx = f[1], gy = f[2], gz = f[3];
-    const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    // forward values with sample_optics' exact arithmetic (same clamp decisions)
-    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, Hgx = 0.f, Hgy = 0.f, Hgz = 0.f, r = 0.f;
-    if (gg > 0.0f) {
-        r = rsqrtf(gg);
-        gmag = gg * r;
-        Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
-        Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
-        Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
-        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) * (r * r);
-        hx = gx * r;
-        hy = gy * r;
-        hz = gz * r;
-    }
-    const float gn = gmag * inv_gmax;
-    const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
-    // transfer-function cell (same arithmetic as tf_lookup)
-    const int w = tp.tf_w, h = tp.tf_h;
-    const float I = f[0];
-    const float xs = fminf(fmaxf(I, 0.0f), 1.0f) * (float)(w - 1);
-    const int j = min((int)xs, w - 2);
-    const float t = xs - (float)j;
-    float4 c, T00, T01, T10 = make_float4(0.f, 0.f, 0.f, 0.f), T11 = T10;
-    int k = 0;
-    float q = 0.0f;
-    T00 = __ldg(tf + j);
-    T01 = __ldg(tf + j + 1);
-    if (h == 1) {
-        c = lerp4(T00, T01, t);
-    } else {
-        const float ys = fminf(fmaxf(y, 0.0f), 1.0f) * (float)(h - 1);
-        k = min((int)ys, h - 2);
-        q = ys - (float)k;
-        const float4* r0 = tf + (long long)k * w + j;
-        T00 = __ldg(r0);
-        T01 = __ldg(r0 + 1);
-        T10 = __ldg(r0 + w);
-        T11 = __ldg(r0 + w + 1);
-        c = lerp4(lerp4(T00, T01, t), lerp4(T10, T11, t), q);
-    }
-    const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
-    const float wi = fmaf(tp.gk, kappa, 1.0f);
-    const float wk = fminf(fmaxf(wi, 0.0f), tp.w_max);
-    const float raw = tp.opacity_scale * c.w * mg * wk;
-    const float dot = fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2]));
-    const float d = fabsf(dot);
+    const float gg = o.gg, r = o.r, kappa = o.kappa, hx = o.hx, hy = o.hy, hz = o.hz;
+    const float Hgx = o.Hgx, Hgy = o.Hgy, Hgz = o.Hgz, gn = o.gn, y = o.y;
+    const int w = tp.tf_w, h = tp.tf_h, j = o.j, k = o.k;
+    const float I = f[0], t = o.t, q = o.q;
+    const float4 c = o.c, T00 = o.T00, T01 = o.T01, T10 = o.T10, T11 = o.T11;
+    const float mg = o.mg, wi = o.wi, wk = o.wk, raw = o.raw, dot = o.dot, d = o.d;
 
     // colour
     float dr[4] = {0.f, 0.f, 0.f, 0.f}, dd = 0.f;

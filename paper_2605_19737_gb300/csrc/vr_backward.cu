@@ -46,10 +46,8 @@ template <bool kDerived>
 __device__ __forceinline__ void eval_field(const VolumeDev& v, long long bi, const int i0[3], const int bc[3], int base,
                                            const float f[3], const float is[3], float fld[10]) {
     if (kDerived) {
-        const int cell =
-            ((i0[2] - kCells * bc[2]) * kDerEdge + (i0[1] - kCells * bc[1])) * kDerEdge + (i0[0] - kCells * bc[0]);
-        field_eval_derived(reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats), cell, f[0], f[1], f[2],
-                           fld);
+        field_eval_derived<true>(reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats), i0[0] & 7, i0[1] & 7,
+                           i0[2] & 7, f[0], f[1], f[2], fld);
     } else {
         field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
         scale_field(fld, is);
@@ -257,15 +255,16 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 eval_field<kDerived>(v, bi, i0, bc, base, f, is, fld);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
-                float alpha, col[3];
-                sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                SampleOptics so;
+                optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
+                const float alpha = so.alpha, col[3] = {so.col[0], so.col[1], so.col[2]};
                 if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
                 const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
                                        g4.w * P);
                 const float ta = Tk * alpha;
                 const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
                 float dfs[10];
-                sample_adjoint(fld, vval, r.dir, L.tp, tf, inv_gmax, da, dc, sink, dp, dfs);
+                sample_adjoint(fld, so, r.dir, L.tp, inv_gmax, da, dc, sink, dp, dfs);
                 if (kDerived && B.dgrad) {
                     scatter_channels(B.dgrad, v.n, i0, f, dfs);
                 } else if (B.dvol) {
@@ -430,15 +429,16 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
                 scale_field(fld, is);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
-                float alpha, col[3];
-                sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
+                SampleOptics so;
+                optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
+                const float alpha = so.alpha, col[3] = {so.col[0], so.col[1], so.col[2]};
                 if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
                 const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
                                        g4.w * P);
                 const float ta = Tk * alpha;
                 const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
                 float dfs[10];
-                sample_adjoint(fld, vval, r.dir, L.tp, tf, inv_gmax, da, dc, sink, dp, dfs);
+                sample_adjoint(fld, so, r.dir, L.tp, inv_gmax, da, dc, sink, dp, dfs);
                 if (B.dvol) {
                     const int lx = i0[0] - kCells * sc[0], ly = i0[1] - kCells * sc[1], lz = i0[2] - kCells * sc[2];
                     lo_t[0] = min(lo_t[0], lx), lo_t[1] = min(lo_t[1], ly), lo_t[2] = min(lo_t[2], lz);

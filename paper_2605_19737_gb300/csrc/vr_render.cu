@@ -44,7 +44,7 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
 // skipping bricks classified empty. Shared by the single-view and batched kernels.
 // With kState it also returns the ray's last sample index (kstop) and the
 // transmittance in front of that sample (t_last), which the adjoint sweep starts from.
-template <bool kDerived, bool kState = false>
+template <bool kDerived, bool kState = false, bool kParity = false>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
                                              float4& out, unsigned& dense, unsigned& evald, int* klast_out = nullptr,
@@ -90,7 +90,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         const int base = (lz * kEdge + ly) * kEdge + lx;
         float fld[10];
         if (kDerived) {
-            field_eval_derived(dbrick, (lz * kDerEdge + ly) * kDerEdge + lx, f[0], f[1], f[2], fld);
+            field_eval_derived<kParity>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld);
         } else {
             field_eval(GlobalLoad{ibrick}, base, f[0], f[1], f[2], fld);
             scale_field(fld, is);

@@ -188,17 +188,29 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
 }
 
 // Sample field from derived bricks: trilinear interpolation of the 10 voxel-wise
-// channels over the cell's 8 corners (already in mm units). `cell` is the local
-// corner index of voxel (i0, j0, k0) within the brick's 9^3 block.
-__device__ __forceinline__ void field_eval_derived(const float4* __restrict__ brick, int cell, float fx, float fy,
-                                                   float fz, float out[10]) {
+// channels over the cell's 8 corners (already in mm units). (lx, ly, lz) is the
+// cell's corner voxel (i0, j0, k0) local to the brick's 9^3 block.
+// kParity: the 8 corner loads are issued in order of the corners' parity (even/odd
+// voxel index per axis) rather than of their offset from the cell, so that lanes in
+// neighbouring cells read the same record in the same instruction and their loads
+// coalesce; each lane picks the matching weight. That costs ~30 instructions per
+// sample; measured, the adjoint sweep gains 3 %, the 1080p forward frame loses
+// 1.3 % (512^2 views gain 3 %). The forward kernels keep the offset order, so that
+// single-view and batched renders stay bit-identical; the adjoint uses parity order.
+template <bool kParity>
+__device__ __forceinline__ void field_eval_derived(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
+                                                   float fy, float fz, float out[10]) {
+    const int px = kParity ? lx & 1 : 0, py = kParity ? ly & 1 : 0, pz = kParity ? lz & 1 : 0;
+    const int base = (lz * kDerEdge + ly) * kDerEdge + lx;
 #pragma unroll
     for (int q = 0; q < 10; ++q) out[q] = 0.0f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        // kParity: the corner of parity (c & 1, c >> 1 & 1, c >> 2 & 1), i.e. offset
+        // parity ^ cell parity; otherwise the corner at offset (c & 1, c >> 1 & 1, c >> 2 & 1)
+        const int dx = px ^ (c & 1), dy = py ^ ((c >> 1) & 1), dz = pz ^ ((c >> 2) & 1);
         const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-        const float4* p = brick + 3 * (cell + (dz * kDerEdge + dy) * kDerEdge + dx);
+        const float4* p = brick + 3 * (base + (dz * kDerEdge + dy) * kDerEdge + dx);
         const float4 a = __ldg(p), m = __ldg(p + 1), t = __ldg(p + 2);
         out[0] = fmaf(w, a.x, out[0]);
         out[1] = fmaf(w, a.y, out[1]);
@@ -231,19 +243,84 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
                        fmaf(t, b.w - a.w, a.w));
 }
 
-// Piecewise-linear transfer function: x over tf_w entries, y over tf_h rows.
-__device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tf, int w, int h, float x, float y) {
-    const float xs = fminf(fmaxf(x, 0.0f), 1.0f) * (float)(w - 1);
-    const int j = min((int)xs, w - 2);
-    const float t = xs - (float)j;
-    if (h == 1) return lerp4(__ldg(tf + j), __ldg(tf + j + 1), t);
-    const float ys = fminf(fmaxf(y, 0.0f), 1.0f) * (float)(h - 1);
-    const int k = min((int)ys, h - 2);
-    const float q = ys - (float)k;
-    const float4* r0 = tf + (long long)k * w + j;
-    const float4 lo = lerp4(__ldg(r0), __ldg(r0 + 1), t);
-    const float4 hi = lerp4(__ldg(r0 + w), __ldg(r0 + w + 1), t);
-    return lerp4(lo, hi, q);
+// Everything one sample's optics compute on the way to its opacity and colour:
+// the forward kernels keep alpha and col, the adjoint reuses the rest.
+struct SampleOptics {
+    float gg, r, gmag, kappa, hx, hy, hz, Hgx, Hgy, Hgz;  // |g|^2, 1/|g|, |g|, Eq. 3, unit normal, H g
+    float gn, y;                                          // |g|/gmax and the second lookup coordinate
+    int j, k;                                             // transfer-function cell
+    float t, q;                                           // and its fractions
+    float4 T00, T01, T10, T11, c;                         // cell entries and the looked-up RGBA
+    float mg, wi, wk, raw, dot, d;                        // Eq. 4 factors, shading cosine
+    float alpha, col[3];
+};
+
+// Opacity (Eq. 4) and colour of one sample from its field (already scaled to
+// mm units) and vesselness value, keeping the intermediate values in `o`.
+__device__ __forceinline__ void optics_core(const float f[10], float vval, const float dir[3], const TissueDev& tp,
+                                            const float4* __restrict__ tf, float inv_gmax, SampleOptics& o) {
+    const float gx = f[1], gy = f[2], gz = f[3];
+    o.gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    o.r = o.gmag = o.kappa = o.hx = o.hy = o.hz = o.Hgx = o.Hgy = o.Hgz = 0.0f;
+    if (o.gg > 0.0f) {
+        // one reciprocal square root gives |g|, the unit normal and 1/|g|^2
+        o.r = rsqrtf(o.gg);
+        o.gmag = o.gg * o.r;
+        o.Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
+        o.Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
+        o.Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
+        o.kappa = fmaf(gx, o.Hgx, fmaf(gy, o.Hgy, gz * o.Hgz)) * (o.r * o.r);
+        o.hx = gx * o.r;
+        o.hy = gy * o.r;
+        o.hz = gz * o.r;
+    }
+    o.gn = o.gmag * inv_gmax;
+    o.y = tp.tf_mode == 1 ? o.gn : (tp.tf_mode == 2 ? vval : 0.0f);
+    // piecewise-linear transfer function: x over tf_w entries, y over tf_h rows
+    const int w = tp.tf_w, h = tp.tf_h;
+    const float xs = fminf(fmaxf(f[0], 0.0f), 1.0f) * (float)(w - 1);
+    o.j = min((int)xs, w - 2);
+    o.t = xs - (float)o.j;
+    if (h == 1) {
+        o.k = 0;
+        o.q = 0.0f;
+        o.T00 = __ldg(tf + o.j);
+        o.T01 = __ldg(tf + o.j + 1);
+        o.T10 = o.T11 = make_float4(0.f, 0.f, 0.f, 0.f);
+        o.c = lerp4(o.T00, o.T01, o.t);
+    } else {
+        const float ys = fminf(fmaxf(o.y, 0.0f), 1.0f) * (float)(h - 1);
+        o.k = min((int)ys, h - 2);
+        o.q = ys - (float)o.k;
+        const float4* r0 = tf + (long long)o.k * w + o.j;
+        o.T00 = __ldg(r0);
+        o.T01 = __ldg(r0 + 1);
+        o.T10 = __ldg(r0 + w);
+        o.T11 = __ldg(r0 + w + 1);
+        o.c = lerp4(lerp4(o.T00, o.T01, o.t), lerp4(o.T10, o.T11, o.t), o.q);
+    }
+    o.mg = tp.grad_mod ? fminf(o.gn, 1.0f) : 1.0f;
+    o.wi = fmaf(tp.gk, o.kappa, 1.0f);
+    o.wk = fminf(fmaxf(o.wi, 0.0f), tp.w_max);
+    o.raw = tp.opacity_scale * o.c.w * o.mg * o.wk;
+    o.alpha = fminf(fmaxf(o.raw, 0.0f), 1.0f);
+    // optional step-size correction 1 - (1 - alpha)^e = -expm1(e log1p(-alpha)): accurate
+    // relative to alpha also for nearly transparent samples
+    if (tp.alpha_exp > 0.0f) o.alpha = -expm1f(tp.alpha_exp * log1pf(-o.alpha));
+    o.dot = fmaf(o.hx, dir[0], fmaf(o.hy, dir[1], o.hz * dir[2]));
+    o.d = fabsf(o.dot);
+    if (tp.shading) {
+        const float d2 = o.d * o.d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;
+        const float lit = fmaf(tp.kd, o.d, tp.ka);
+        const float spec = tp.ks * d16;
+        o.col[0] = fmaf(o.c.x, lit, spec);
+        o.col[1] = fmaf(o.c.y, lit, spec);
+        o.col[2] = fmaf(o.c.z, lit, spec);
+    } else {
+        o.col[0] = o.c.x;
+        o.col[1] = o.c.y;
+        o.col[2] = o.c.z;
+    }
 }
 
 // Opacity (Eq. 4) and colour of one sample from its field (already scaled to
@@ -251,43 +328,12 @@ __device__ __forceinline__ float4 tf_lookup(const float4* __restrict__ tf, int w
 __device__ __forceinline__ void sample_optics(const float f[10], float vval, const float dir[3], const TissueDev& tp,
                                               const float4* __restrict__ tf, float inv_gmax, float& alpha,
                                               float col[3]) {
-    const float gx = f[1], gy = f[2], gz = f[3];
-    const float gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    float gmag = 0.f, kappa = 0.f, hx = 0.f, hy = 0.f, hz = 0.f;
-    if (gg > 0.0f) {
-        // one reciprocal square root gives |g|, the unit normal and 1/|g|^2
-        const float r = rsqrtf(gg);
-        gmag = gg * r;
-        const float Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
-        const float Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
-        const float Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
-        kappa = fmaf(gx, Hgx, fmaf(gy, Hgy, gz * Hgz)) * (r * r);
-        hx = gx * r;
-        hy = gy * r;
-        hz = gz * r;
-    }
-    const float gn = gmag * inv_gmax;
-    const float y = tp.tf_mode == 1 ? gn : (tp.tf_mode == 2 ? vval : 0.0f);
-    const float4 c = tf_lookup(tf, tp.tf_w, tp.tf_h, f[0], y);
-    const float mg = tp.grad_mod ? fminf(gn, 1.0f) : 1.0f;
-    const float wk = fminf(fmaxf(fmaf(tp.gk, kappa, 1.0f), 0.0f), tp.w_max);
-    alpha = fminf(fmaxf(tp.opacity_scale * c.w * mg * wk, 0.0f), 1.0f);
-    // optional step-size correction 1 - (1 - alpha)^e = -expm1(e log1p(-alpha)): accurate
-    // relative to alpha also for nearly transparent samples
-    if (tp.alpha_exp > 0.0f) alpha = -expm1f(tp.alpha_exp * log1pf(-alpha));
-    if (tp.shading) {
-        const float d = fabsf(fmaf(hx, dir[0], fmaf(hy, dir[1], hz * dir[2])));
-        const float d2 = d * d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;
-        const float lit = fmaf(tp.kd, d, tp.ka);
-        const float spec = tp.ks * d16;
-        col[0] = fmaf(c.x, lit, spec);
-        col[1] = fmaf(c.y, lit, spec);
-        col[2] = fmaf(c.z, lit, spec);
-    } else {
-        col[0] = c.x;
-        col[1] = c.y;
-        col[2] = c.z;
-    }
+    SampleOptics o;
+    optics_core(f, vval, dir, tp, tf, inv_gmax, o);
+    alpha = o.alpha;
+    col[0] = o.col[0];
+    col[1] = o.col[1];
+    col[2] = o.col[2];
 }
 
 // Divide the raw stencil sums by the spacing (gradient) and spacing products (Hessian).
