@@ -3,7 +3,8 @@
     python -m paper_2605_19737_gb300.profile_run --workload brainweb_1080p --kernel gather --frames 3
 
 Workloads: brainweb_1080p (181x217x181 uint16, 1920x1080), brainweb_540p (same
-volume, 960x540), head64 (64^3 float32, 128x128). Prints the mean frame time
+volume, 960x540), head64 (64^3 float32, 128x128), diff_head128_8cam (128^3
+float32, 8 cameras at 512x512). Prints the mean frame time
 from CUDA events (a number taken under a profiler is not a benchmark value).
 """
 
@@ -23,7 +24,8 @@ def main():
     from phantoms import workloads
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="brainweb_1080p", choices=["brainweb_1080p", "brainweb_540p", "head64"])
+    ap.add_argument("--workload", default="brainweb_1080p",
+                    choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam"])
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=4)
@@ -32,6 +34,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "head64":
         case = workloads.head64_128px()
+    elif args.workload == "diff_head128_8cam":
+        case = workloads.diff_head128_8cam()
     elif args.workload == "brainweb_540p":
         case = workloads.brainweb_1080p(width=960, height=540)
     else:
