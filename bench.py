@@ -48,8 +48,8 @@ FLOPS_PER_SAMPLE = {"gather": 124 + 179, "stencil": 124 + 383, "staged": 124 + 3
 # Bytes of one brick: derived (9^3 corners x 12 float32) or intensity (12^3 float32).
 BRICK_BYTES = {"gather": 9 * 9 * 9 * 12 * 4, "stencil": 12 ** 3 * 4, "staged": 12 ** 3 * 4}
 DERIVED_BUDGET_BYTES = 16 << 30
-KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_gb300/csrc/vr_sample.cuh",
-                  "paper_2605_19737_gb300/csrc/vr_internal.cuh")
+KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_gb300/csrc/vr_march.cuh",
+                  "paper_2605_19737_gb300/csrc/vr_sample.cuh", "paper_2605_19737_gb300/csrc/vr_internal.cuh")
 
 
 def kernel_source_hash():

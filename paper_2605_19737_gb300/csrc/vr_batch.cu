@@ -1,0 +1,84 @@
+// vr_batch.cu -- batched persistent forward raymarch over many views (uneven
+// volumes x cameras) from one work queue, one launch (optionally graph-captured).
+#include "vr_march.cuh"
+
+namespace vr {
+
+namespace {
+
+// Batched persistent renderer: every warp pulls packet_w x packet_h ray packets
+// from one work queue spanning all views (each view: its own volume, uniforms,
+// transfer function, camera, output and size). A packet's view is found by
+// binary search over the views' packet prefix sums. kAllDerived: every view's
+// volume has derived bricks, so only that path is compiled in and the kernel is
+// held to 72 registers (measured: 110 Gsamples/s on the 256-view batch, against
+// 102 at 64 registers); otherwise each view takes its own path at run time.
+template <bool kAllDerived>
+__device__ __forceinline__ void batch_body(const BatchLaunch& B) {
+    const int lane = threadIdx.x & 31;
+    unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0;
+    while (true) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(B.work_counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned)B.n_work) break;
+        int lo = 0, hi = B.n_views - 1;  // last view with prefix <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((unsigned)__ldg(B.packet_prefix + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const ViewDev& vw = B.views[lo];
+        const int local = (int)item - __ldg(B.packet_prefix + lo);
+        const int npx = (vw.W + B.packet_w - 1) / B.packet_w;
+        const int px = local % npx, py = local / npx;
+        const int i = px * B.packet_w + lane % B.packet_w, j = py * B.packet_h + lane / B.packet_w;
+        const bool inside = i < vw.W && j < vw.H;
+        const VolumeDev& v = vw.vol;
+        const float gmax = __ldg(&v.vc->gmax);
+        const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+        const float is[3] = {1.0f / v.s[0], 1.0f / v.s[1], 1.0f / v.s[2]};
+        RayDev r;
+        const bool hit = inside && setup_ray(vw.cam, vw.rc, i, j, v.n, v.s, r);
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned dense = 0, evald = 0;
+        if (hit) {
+            if (kAllDerived || v.dbricks)
+                march_gather<true>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
+                                   dense, evald);
+            else
+                march_gather<false>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
+                                    dense, evald);
+        }
+        if (inside) reinterpret_cast<float4*>(vw.out)[(long long)j * vw.W + i] = out;
+        rays_hit += hit ? 1u : 0u;
+        dense_tot += dense;
+        eval_tot += evald;
+    }
+    if (B.counters) add_counters(B.counters, rays_hit, dense_tot, eval_tot, 0u);
+}
+
+__global__ void __maxnreg__(72) k_render_batch_derived(const __grid_constant__ BatchLaunch B) { batch_body<true>(B); }
+
+__global__ void __launch_bounds__(256, 3) k_render_batch_mixed(const __grid_constant__ BatchLaunch B) {
+    batch_body<false>(B);
+}
+
+}  // namespace
+
+cudaError_t batch_ctas_per_sm(int warps_per_block, bool all_derived, int* per_sm) {
+    return all_derived
+               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_derived, warps_per_block * 32, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_mixed, warps_per_block * 32, 0);
+}
+
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,
+                                cudaStream_t st) {
+    if (all_derived)
+        k_render_batch_derived<<<ctas, warps_per_block * 32, 0, st>>>(B);
+    else
+        k_render_batch_mixed<<<ctas, warps_per_block * 32, 0, st>>>(B);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

@@ -50,15 +50,17 @@ def main():
         ctx.set_tissue_params(vid, case["tf"], **case["params"])
         out = torch.empty((case["cams"].shape[0], case["H"], case["W"], 4), device="cuda")
         dl = torch.randn(out.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+        # with --backward the forward records the per-ray state the backward starts from
+        state = torch.empty(out.shape[:3] + (2,), device="cuda") if args.backward else None
         ts, tb = [], []
         for _ in range(args.frames):
             s, e, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             s.record()
             ctx.render(vid, case["cams"], case["W"], case["H"], out=out, kernel=kernel, packet_w=args.packet_w,
-                       warps_per_block=args.warps)
+                       warps_per_block=args.warps, ray_state=state)
             e.record()
             if args.backward:
-                ctx.render_backward(vid, case["cams"], case["W"], case["H"], dl, kernel=kernel)
+                ctx.render_backward(vid, case["cams"], case["W"], case["H"], dl, kernel=kernel, ray_state=state)
             b.record()
             ctx.synchronize()
             ts.append(s.elapsed_time(e))
