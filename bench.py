@@ -37,14 +37,19 @@ sys.path.insert(0, ROOT)
 METRIC = "Gsamples/s & FPS at 1080p (fwd, fwd+bwd) vs plain fwd, % of HBM roofline"
 UNIT = "Gsamples/s"
 L2_FLUSH_BYTES = 256 << 20
-# FP32 operations of one evaluated sample of the raymarch, counted from the
-# algorithm. Shared by all kernels: curvature/normalisation (38), transfer
-# function (2D bilinear, 36), Eq. 4 (8), Phong (16), Eqs. 5-6 (8), position (18)
-# = 124. Field at the sample: from the derived bricks (voxel-wise I, gradient,
-# Hessian), trilinear weights (19) + 8 corners x 10 channels FMA (160) = 179; by
-# the per-sample stencils, the 56-voxel separable contraction (368 incl. the
-# 4-tap weights) + spacing scale (15) = 383.
-FLOPS_PER_SAMPLE = {"gather": 124 + 179, "stencil": 124 + 383, "staged": 124 + 383}
+# FP32 operations per sample of the raymarch, counted from the algorithm.
+# Derived bricks (voxel-wise I, gradient, Hessian), in two stages:
+#   every evaluated sample: position (18), trilinear weights (19), 8 corners x
+#   (I, g) FMA (64), |g| and the unit normal (11), 2D bilinear transfer function
+#   (36) = 148;
+#   samples with a non-zero transfer-function opacity ("shaded") also: 8 corners x
+#   6 Hessian channels FMA (96), curvature (27), Eq. 4 (8), Phong (16), Eqs. 5-6 (8)
+#   = 155 (303 in all).
+# Per-sample stencils (stencil and staged kernels; every evaluated sample shaded):
+# the 56-voxel separable contraction (368 incl. the 4-tap weights) + spacing scale
+# (15) in place of the 179 of the derived interpolation: 124 + 383 = 507.
+FLOPS_STAGE1 = {"gather": 148, "stencil": 0, "staged": 0}
+FLOPS_SHADED = {"gather": 155, "stencil": 507, "staged": 507}
 # Bytes of one brick: derived (9^3 corners x 12 float32) or intensity (12^3 float32).
 BRICK_BYTES = {"gather": 9 * 9 * 9 * 12 * 4, "stencil": 12 ** 3 * 4, "staged": 12 ** 3 * 4}
 DERIVED_BUDGET_BYTES = 16 << 30
@@ -312,7 +317,7 @@ def run(args):
     ctr = pkg.new_counters(local)
     ctx.render(vid, case["cams"], W, H, out=out, counters=ctr)
     torch.cuda.synchronize()
-    rays, dense, evald = [int(x) for x in ctr.cpu().numpy()[:3]]
+    rays, dense, evald, _, shaded = [int(x) for x in ctr.cpu().numpy()[:5]]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
@@ -449,7 +454,8 @@ def run(args):
     fp32_nominal = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     fma_ms, fma_flops = ctx.fma_peak()
     fp32_peak = fma_flops / 1e12
-    achieved_tflops = evald * FLOPS_PER_SAMPLE[kind] / (ms * 1e-3) / 1e12
+    frame_flops = evald * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
+    achieved_tflops = frame_flops / (ms * 1e-3) / 1e12
     if rank == 0:
         cb = None
         if ws == 1 and not args.no_cpu_baseline:
@@ -464,10 +470,12 @@ def run(args):
                        "step_vox": 0.5, "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fps": 1000.0 / ms, "fps_wall": fps_wall,
-            "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "rays": rays},
+            "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "shaded_per_frame": shaded,
+                        "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "flops_per_evaluated_sample": FLOPS_PER_SAMPLE[kind],
+                         "flops_per_frame": frame_flops,
+                         "flops_per_sample": {"evaluated": FLOPS_STAGE1[kind], "shaded": FLOPS_SHADED[kind]},
                          "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
                          "peak_source": "measured: FP32 FMA probe vr_fma_peak (8 independent chains per thread, "
                                         "%.3f ms per launch); nominal 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"

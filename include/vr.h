@@ -99,6 +99,10 @@ typedef struct {
     unsigned long long dense_samples;     /* sample points up to each ray's stop */
     unsigned long long evaluated_samples; /* of those, not in skipped bricks */
     unsigned long long bricks_staged;     /* brick copies into shared memory */
+    unsigned long long shaded_samples;    /* of the evaluated, those whose transfer-function
+                                             opacity was non-zero, so that the Hessian, Eq. 4
+                                             and the shading were computed (the others add
+                                             nothing; all of them for the stencil kernels) */
 } vr_counters;
 
 typedef enum {

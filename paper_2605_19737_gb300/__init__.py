@@ -320,6 +320,6 @@ def nifti_info(path):
 
 
 def new_counters(device=0):
-    """Zeroed device vr_counters as a (4,) int64 tensor (rays, dense, evaluated, staged)."""
+    """Zeroed device vr_counters as a (5,) int64 tensor (rays, dense, evaluated, staged, shaded)."""
     torch = _torch()
-    return torch.zeros(4, dtype=torch.int64, device="cuda:%d" % device)
+    return torch.zeros(5, dtype=torch.int64, device="cuda:%d" % device)

@@ -17,16 +17,18 @@ __device__ __forceinline__ int brick_index(const VolumeDev& v, const int b[3]) {
 }
 
 __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, unsigned dense, unsigned evald,
-                                             unsigned staged) {
+                                             unsigned staged, unsigned shaded) {
     const unsigned r = __reduce_add_sync(0xffffffffu, rays);
     const unsigned d = __reduce_add_sync(0xffffffffu, dense);
     const unsigned e = __reduce_add_sync(0xffffffffu, evald);
     const unsigned s = __reduce_add_sync(0xffffffffu, staged);
+    const unsigned h = __reduce_add_sync(0xffffffffu, shaded);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&ctr->rays, (unsigned long long)r);
         atomicAdd(&ctr->dense_samples, (unsigned long long)d);
         atomicAdd(&ctr->evaluated_samples, (unsigned long long)e);
         atomicAdd(&ctr->bricks_staged, (unsigned long long)s);
+        atomicAdd(&ctr->shaded_samples, (unsigned long long)h);
     }
 }
 
@@ -37,15 +39,15 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
 template <bool kDerived, bool kState = false, bool kParity = false>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
-                                             float4& out, unsigned& dense, unsigned& evald, int* klast_out = nullptr,
-                                             float* t_last = nullptr) {
+                                             float4& out, unsigned& dense, unsigned& evald, unsigned& shaded,
+                                             int* klast_out = nullptr, float* t_last = nullptr) {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
     float A_prev = 0.f;  // kState: A before the last evaluated sample
     int klast = -1;      // kState: last evaluated sample
     int k1 = -1;         // kState: first sample with A >= 1 (where the adjoint sweep must start
     float T1 = 1.f;      // when early termination is off) and the transmittance in front of it
     int k = 0, kstop = -1;
-    unsigned ne = 0;
+    unsigned ne = 0, nsh = 0;
     // The skip flag and the base pointers of the current brick are re-read only
     // when the brick changes (about every 16 samples), keeping a dependent L1 round
     // trip and the 64-bit address arithmetic off the path of every sample.
@@ -78,17 +80,33 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         // local cell of (i0, j0, k0) within the brick: i0 - 8 bc = i0 & 7
         const int lx = i0[0] & 7, ly = i0[1] & 7, lz = i0[2] & 7;
         const int base = (lz * kEdge + ly) * kEdge + lx;
-        float fld[10];
+        const float vval =
+            v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
+        float fld[10], alpha, col[3];
         if (kDerived) {
-            field_eval_derived<kParity>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld);
+            // I and the gradient first (one 16-byte load per corner), then the transfer
+            // function: a zero opacity entry makes alpha exactly 0 whatever the Hessian,
+            // and the sample adds nothing (bit-neutral), so its Hessian is never read
+            derived_channels<kParity, 0, 4>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld);
+            SampleOptics o;
+            optics_tf(fld, vval, tp, tf, inv_gmax, o);
+            if (o.c.w == 0.0f) {
+                ++ne;
+                ++k;
+                continue;
+            }
+            derived_channels<kParity, 4, 6>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld + 4);
+            optics_rest(fld, r.dir, tp, o);
+            alpha = o.alpha;
+            col[0] = o.col[0];
+            col[1] = o.col[1];
+            col[2] = o.col[2];
         } else {
             field_eval(GlobalLoad{ibrick}, base, f[0], f[1], f[2], fld);
             scale_field(fld, is);
+            sample_optics(fld, vval, r.dir, tp, tf, inv_gmax, alpha, col);
         }
-        const float vval =
-            v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
-        float alpha, col[3];
-        sample_optics(fld, vval, r.dir, tp, tf, inv_gmax, alpha, col);
+        ++nsh;
         const float wgt = (1.0f - A) * alpha;  // Eqs. 5-6
         C0 = fmaf(col[0], wgt, C0);
         C1 = fmaf(col[1], wgt, C1);
@@ -112,6 +130,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     out = make_float4(C0, C1, C2, A);
     dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;
     evald = ne;
+    shaded = nsh;
     if (kState) {
         // the adjoint sweep starts at the first sample with A >= min(et, 1): the stopping
         // sample, or (early termination off) the first that made A reach 1

@@ -16,10 +16,10 @@ namespace vr {
 
 namespace {
 
-// 8 resident CTAs per SM for the derived-brick path (<= 64 registers; measured 1.7 %
-// faster at 1080p than 7 CTAs at 72 registers despite a few spills), 6 for the stencils.
+// 7 resident CTAs per SM for the derived-brick path (<= 72 registers; at 1080p 2.46 ms
+// against 2.53 ms for 8 CTAs at 64 registers), 6 for the stencils.
 template <bool kDerived, bool kState>
-__global__ void __launch_bounds__(128, kDerived ? 8 : 6) k_render_gather(const __grid_constant__ RenderLaunch L) {
+__global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
     tile_pixel(L.packet_w, w, l, di, dj);
@@ -36,10 +36,10 @@ __global__ void __launch_bounds__(128, kDerived ? 8 : 6) k_render_gather(const _
     RayDev r;
     const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned dense = 0, evald = 0;
+    unsigned dense = 0, evald = 0, shaded = 0;
     int kl = -1;
     float tl = 1.0f;
-    if (hit) march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, &kl, &tl);
+    if (hit) march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, shaded, &kl, &tl);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         reinterpret_cast<float4*>(L.out)[pix] = px;
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(128, kDerived ? 8 : 6) k_render_gather(const _
             L.ray_samples[2 * pix + 1] = evald;
         }
     }
-    if (L.counters) add_counters(L.counters, hit ? 1u : 0u, dense, evald, 0u);
+    if (L.counters) add_counters(L.counters, hit ? 1u : 0u, dense, evald, 0u, shaded);
 }
 
 }  // namespace
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
         dense_tot += dense;
         eval_tot += evald;
     }
-    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u);
+    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u, eval_tot);
 }
 
 }  // namespace

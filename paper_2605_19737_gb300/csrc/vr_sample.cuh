@@ -187,6 +187,44 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
     out[9] = hyz;
 }
 
+// Channels [kFirst, kFirst + kCount) of the derived field at the sample: kFirst = 0,
+// kCount = 4 reads (I, gx, gy, gz) -- the first 16-byte vector of each corner;
+// kFirst = 4, kCount = 6 the Hessian -- the second and third. Each channel sums its
+// 8 corners in the same order, so split and whole evaluations agree bit for bit.
+template <bool kParity, int kFirst, int kCount>
+__device__ __forceinline__ void derived_channels(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
+                                                 float fy, float fz, float* out) {
+    const int px = kParity ? lx & 1 : 0, py = kParity ? ly & 1 : 0, pz = kParity ? lz & 1 : 0;
+    const int base = (lz * kDerEdge + ly) * kDerEdge + lx;
+#pragma unroll
+    for (int q = 0; q < kCount; ++q) out[q] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        // kParity: the corner of parity (c & 1, c >> 1 & 1, c >> 2 & 1), i.e. offset
+        // parity ^ cell parity; otherwise the corner at offset (c & 1, c >> 1 & 1, c >> 2 & 1)
+        const int dx = px ^ (c & 1), dy = py ^ ((c >> 1) & 1), dz = pz ^ ((c >> 2) & 1);
+        const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+        const float4* p = brick + 3 * (base + (dz * kDerEdge + dy) * kDerEdge + dx);
+        if (kFirst == 0) {
+            const float4 a = __ldg(p);
+            out[0] = fmaf(w, a.x, out[0]);
+            out[1] = fmaf(w, a.y, out[1]);
+            out[2] = fmaf(w, a.z, out[2]);
+            out[3] = fmaf(w, a.w, out[3]);
+        }
+        if (kFirst + kCount > 4) {
+            const float4 m = __ldg(p + 1), t = __ldg(p + 2);
+            float* o = out + (4 - kFirst);
+            o[0] = fmaf(w, m.x, o[0]);
+            o[1] = fmaf(w, m.y, o[1]);
+            o[2] = fmaf(w, m.z, o[2]);
+            o[3] = fmaf(w, m.w, o[3]);
+            o[4] = fmaf(w, t.x, o[4]);
+            o[5] = fmaf(w, t.y, o[5]);
+        }
+    }
+}
+
 // Sample field from derived bricks: trilinear interpolation of the 10 voxel-wise
 // channels over the cell's 8 corners (already in mm units). (lx, ly, lz) is the
 // cell's corner voxel (i0, j0, k0) local to the brick's 9^3 block.
@@ -200,29 +238,7 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
 template <bool kParity>
 __device__ __forceinline__ void field_eval_derived(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
                                                    float fy, float fz, float out[10]) {
-    const int px = kParity ? lx & 1 : 0, py = kParity ? ly & 1 : 0, pz = kParity ? lz & 1 : 0;
-    const int base = (lz * kDerEdge + ly) * kDerEdge + lx;
-#pragma unroll
-    for (int q = 0; q < 10; ++q) out[q] = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        // kParity: the corner of parity (c & 1, c >> 1 & 1, c >> 2 & 1), i.e. offset
-        // parity ^ cell parity; otherwise the corner at offset (c & 1, c >> 1 & 1, c >> 2 & 1)
-        const int dx = px ^ (c & 1), dy = py ^ ((c >> 1) & 1), dz = pz ^ ((c >> 2) & 1);
-        const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-        const float4* p = brick + 3 * (base + (dz * kDerEdge + dy) * kDerEdge + dx);
-        const float4 a = __ldg(p), m = __ldg(p + 1), t = __ldg(p + 2);
-        out[0] = fmaf(w, a.x, out[0]);
-        out[1] = fmaf(w, a.y, out[1]);
-        out[2] = fmaf(w, a.z, out[2]);
-        out[3] = fmaf(w, a.w, out[3]);
-        out[4] = fmaf(w, m.x, out[4]);
-        out[5] = fmaf(w, m.y, out[5]);
-        out[6] = fmaf(w, m.z, out[6]);
-        out[7] = fmaf(w, m.w, out[7]);
-        out[8] = fmaf(w, t.x, out[8]);
-        out[9] = fmaf(w, t.y, out[9]);
-    }
+    derived_channels<kParity, 0, 10>(brick, lx, ly, lz, fx, fy, fz, out);
 }
 
 // Trilinear value only (the vesselness channel): 8 corner voxels of the cell.
@@ -255,21 +271,18 @@ struct SampleOptics {
     float alpha, col[3];
 };
 
-// Opacity (Eq. 4) and colour of one sample from its field (already scaled to
-// mm units) and vesselness value, keeping the intermediate values in `o`.
-__device__ __forceinline__ void optics_core(const float f[10], float vval, const float dir[3], const TissueDev& tp,
-                                            const float4* __restrict__ tf, float inv_gmax, SampleOptics& o) {
+// First half of a sample's optics, from I and the gradient alone (f[0..3]): |g|,
+// the unit normal, the lookup coordinates and the transfer-function RGBA. Its
+// opacity entry c.w decides whether the sample can be visible at all.
+__device__ __forceinline__ void optics_tf(const float f[4], float vval, const TissueDev& tp,
+                                          const float4* __restrict__ tf, float inv_gmax, SampleOptics& o) {
     const float gx = f[1], gy = f[2], gz = f[3];
     o.gg = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    o.r = o.gmag = o.kappa = o.hx = o.hy = o.hz = o.Hgx = o.Hgy = o.Hgz = 0.0f;
+    o.r = o.gmag = o.hx = o.hy = o.hz = 0.0f;
     if (o.gg > 0.0f) {
         // one reciprocal square root gives |g|, the unit normal and 1/|g|^2
         o.r = rsqrtf(o.gg);
         o.gmag = o.gg * o.r;
-        o.Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
-        o.Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
-        o.Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
-        o.kappa = fmaf(gx, o.Hgx, fmaf(gy, o.Hgy, gz * o.Hgz)) * (o.r * o.r);
         o.hx = gx * o.r;
         o.hy = gy * o.r;
         o.hz = gz * o.r;
@@ -299,6 +312,19 @@ __device__ __forceinline__ void optics_core(const float f[10], float vval, const
         o.T11 = __ldg(r0 + w + 1);
         o.c = lerp4(lerp4(o.T00, o.T01, o.t), lerp4(o.T10, o.T11, o.t), o.q);
     }
+}
+
+// Second half: curvature (Eq. 3) from the Hessian f[4..9], Eq. 4 opacity, shading.
+__device__ __forceinline__ void optics_rest(const float f[10], const float dir[3], const TissueDev& tp,
+                                            SampleOptics& o) {
+    const float gx = f[1], gy = f[2], gz = f[3];
+    o.kappa = o.Hgx = o.Hgy = o.Hgz = 0.0f;
+    if (o.gg > 0.0f) {
+        o.Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
+        o.Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
+        o.Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
+        o.kappa = fmaf(gx, o.Hgx, fmaf(gy, o.Hgy, gz * o.Hgz)) * (o.r * o.r);
+    }
     o.mg = tp.grad_mod ? fminf(o.gn, 1.0f) : 1.0f;
     o.wi = fmaf(tp.gk, o.kappa, 1.0f);
     o.wk = fminf(fmaxf(o.wi, 0.0f), tp.w_max);
@@ -321,6 +347,14 @@ __device__ __forceinline__ void optics_core(const float f[10], float vval, const
         o.col[1] = o.c.y;
         o.col[2] = o.c.z;
     }
+}
+
+// Opacity (Eq. 4) and colour of one sample from its field (already scaled to
+// mm units) and vesselness value, keeping the intermediate values in `o`.
+__device__ __forceinline__ void optics_core(const float f[10], float vval, const float dir[3], const TissueDev& tp,
+                                            const float4* __restrict__ tf, float inv_gmax, SampleOptics& o) {
+    optics_tf(f, vval, tp, tf, inv_gmax, o);
+    optics_rest(f, dir, tp, o);
 }
 
 // Opacity (Eq. 4) and colour of one sample from its field (already scaled to
