@@ -95,7 +95,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
                 ++k;
                 continue;
             }
-            derived_channels<kParity, 4, 6>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld + 4);
+            load_hessian<kParity>(tp, dbrick, lx, ly, lz, f, fld);
             optics_rest(fld, r.dir, tp, o);
             alpha = o.alpha;
             col[0] = o.col[0];

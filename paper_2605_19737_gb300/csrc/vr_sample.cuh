@@ -187,10 +187,20 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
     out[9] = hyz;
 }
 
-// Channels [kFirst, kFirst + kCount) of the derived field at the sample: kFirst = 0,
-// kCount = 4 reads (I, gx, gy, gz) -- the first 16-byte vector of each corner;
-// kFirst = 4, kCount = 6 the Hessian -- the second and third. Each channel sums its
-// 8 corners in the same order, so split and whole evaluations agree bit for bit.
+// Sample field from derived bricks: trilinear interpolation of voxel-wise channels
+// (already in mm units) over the cell's 8 corners; (lx, ly, lz) is the cell's corner
+// voxel (i0, j0, k0) local to the brick's 9^3 block. Channels [kFirst, kFirst +
+// kCount): kFirst = 0, kCount = 4 reads (I, gx, gy, gz) -- the first 16-byte vector
+// of each corner; kFirst = 4, kCount = 6 the Hessian (Hxx, Hyy, Hzz, Hxy, Hxz, Hyz)
+// -- the second and third. Each channel sums its 8 corners in the same order, so
+// split and whole evaluations agree bit for bit.
+// kParity: the 8 corner loads are issued in order of the corners' parity (even/odd
+// voxel index per axis) rather than of their offset from the cell, so that lanes in
+// neighbouring cells read the same record in the same instruction and their loads
+// coalesce; each lane picks the matching weight. That costs ~30 instructions per
+// sample; measured, the adjoint sweep gains 3 %, the 1080p forward frame loses
+// 1.3 % (512^2 views gain 3 %). The forward kernels keep the offset order, so that
+// single-view and batched renders stay bit-identical; the adjoint uses parity order.
 template <bool kParity, int kFirst, int kCount>
 __device__ __forceinline__ void derived_channels(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
                                                  float fy, float fz, float* out) {
@@ -225,21 +235,21 @@ __device__ __forceinline__ void derived_channels(const float4* __restrict__ bric
     }
 }
 
-// Sample field from derived bricks: trilinear interpolation of the 10 voxel-wise
-// channels over the cell's 8 corners (already in mm units). (lx, ly, lz) is the
-// cell's corner voxel (i0, j0, k0) local to the brick's 9^3 block.
-// kParity: the 8 corner loads are issued in order of the corners' parity (even/odd
-// voxel index per axis) rather than of their offset from the cell, so that lanes in
-// neighbouring cells read the same record in the same instruction and their loads
-// coalesce; each lane picks the matching weight. That costs ~30 instructions per
-// sample; measured, the adjoint sweep gains 3 %, the 1080p forward frame loses
-// 1.3 % (512^2 views gain 3 %). The forward kernels keep the offset order, so that
-// single-view and batched renders stay bit-identical; the adjoint uses parity order.
+// The Hessian channels fld[4..9] of the derived field -- or zeros when the opacity
+// has no curvature term (gamma = 0): the Hessian then enters nothing (w(kappa) =
+// fma(0, kappa, 1) = 1 for any kappa, and every Hessian gradient carries the factor
+// gamma), so results are unchanged and its 16 loads per sample are saved.
 template <bool kParity>
-__device__ __forceinline__ void field_eval_derived(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
-                                                   float fy, float fz, float out[10]) {
-    derived_channels<kParity, 0, 10>(brick, lx, ly, lz, fx, fy, fz, out);
+__device__ __forceinline__ void load_hessian(const TissueDev& tp, const float4* __restrict__ brick, int lx, int ly,
+                                             int lz, const float f[3], float fld[10]) {
+    if (tp.gk != 0.0f) {
+        derived_channels<kParity, 4, 6>(brick, lx, ly, lz, f[0], f[1], f[2], fld + 4);
+    } else {
+#pragma unroll
+        for (int q = 4; q < 10; ++q) fld[q] = 0.0f;
+    }
 }
+
 
 // Trilinear value only (the vesselness channel): 8 corner voxels of the cell.
 template <class Load>
