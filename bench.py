@@ -39,7 +39,8 @@ UNIT = "Gsamples/s"
 L2_FLUSH_BYTES = 256 << 20
 # FP32 operations per sample of the raymarch, counted from the algorithm.
 # Derived bricks (voxel-wise I, gradient, Hessian), in two stages:
-#   every evaluated sample: position (18), trilinear weights (19), 8 corners x
+#   every interpolated sample (evaluated, and not in a cell classified empty):
+#   position (18), trilinear weights (19), 8 corners x
 #   (I, g) FMA (64), |g| and the unit normal (11), 2D bilinear transfer function
 #   (36) = 148;
 #   samples with a non-zero transfer-function opacity ("shaded") also: 8 corners x
@@ -317,7 +318,7 @@ def run(args):
     ctr = pkg.new_counters(local)
     ctx.render(vid, case["cams"], W, H, out=out, counters=ctr)
     torch.cuda.synchronize()
-    rays, dense, evald, _, shaded = [int(x) for x in ctr.cpu().numpy()[:5]]
+    rays, dense, evald, _, shaded, interp = [int(x) for x in ctr.cpu().numpy()[:6]]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
@@ -454,7 +455,7 @@ def run(args):
     fp32_nominal = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     fma_ms, fma_flops = ctx.fma_peak()
     fp32_peak = fma_flops / 1e12
-    frame_flops = evald * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
+    frame_flops = interp * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
     achieved_tflops = frame_flops / (ms * 1e-3) / 1e12
     if rank == 0:
         cb = None
@@ -470,12 +471,12 @@ def run(args):
                        "step_vox": 0.5, "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "fps": 1000.0 / ms, "fps_wall": fps_wall,
-            "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "shaded_per_frame": shaded,
-                        "rays": rays},
+            "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "interpolated_per_frame": interp,
+                        "shaded_per_frame": shaded, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                          "flops_per_frame": frame_flops,
-                         "flops_per_sample": {"evaluated": FLOPS_STAGE1[kind], "shaded": FLOPS_SHADED[kind]},
+                         "flops_per_sample": {"interpolated": FLOPS_STAGE1[kind], "shaded": FLOPS_SHADED[kind]},
                          "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
                          "peak_source": "measured: FP32 FMA probe vr_fma_peak (8 independent chains per thread, "
                                         "%.3f ms per launch); nominal 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"

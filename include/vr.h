@@ -103,6 +103,9 @@ typedef struct {
                                              opacity was non-zero, so that the Hessian, Eq. 4
                                              and the shading were computed (the others add
                                              nothing; all of them for the stencil kernels) */
+    unsigned long long interpolated_samples; /* of the evaluated, those whose field was read:
+                                             all but the ones in cells classified empty (the
+                                             derived-brick path skips those cells, bit-neutral) */
 } vr_counters;
 
 typedef enum {

@@ -320,6 +320,7 @@ def nifti_info(path):
 
 
 def new_counters(device=0):
-    """Zeroed device vr_counters as a (5,) int64 tensor (rays, dense, evaluated, staged, shaded)."""
+    """Zeroed device vr_counters as a (6,) int64 tensor (rays, dense, evaluated, staged, shaded,
+    interpolated)."""
     torch = _torch()
-    return torch.zeros(5, dtype=torch.int64, device="cuda:%d" % device)
+    return torch.zeros(6, dtype=torch.int64, device="cuda:%d" % device)

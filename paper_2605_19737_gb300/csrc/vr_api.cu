@@ -34,6 +34,8 @@ struct Volume {
     float* d_vessel = nullptr;
     float* d_vbricks = nullptr;
     float* d_dbricks = nullptr;  // derived bricks (voxel-wise I, gradient, Hessian) or nullptr
+    uint16_t* d_cellq = nullptr;     // with the derived bricks: per-cell quantised min/max
+    uint32_t* d_cellmask = nullptr;  // and per-cell empty bits under the current transfer function
     float* d_smax = nullptr;  // per-scale max Hessian norm (8 floats)
     float* d_tf = nullptr;
     size_t tf_cap = 0;
@@ -123,6 +125,8 @@ void free_volume(Volume* v) {
     cudaFree(v->d_vessel);
     cudaFree(v->d_vbricks);
     cudaFree(v->d_dbricks);
+    cudaFree(v->d_cellq);
+    cudaFree(v->d_cellmask);
     cudaFree(v->d_smax);
     cudaFree(v->d_tf);
     cudaFree(v->d_prefix);
@@ -169,6 +173,7 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
     L.vol.bricks = v->d_bricks;
     L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
     L.vol.dbricks = v->d_dbricks;
+    L.vol.cellmask = v->d_cellmask;
     L.vol.empty = v->d_empty;
     L.vol.vc = v->d_vc;
     L.tp = v->tp;
@@ -181,7 +186,21 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
     CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
     CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
-    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    if (v->d_dbricks) {
+        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+        CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
+    }
+    return VR_OK;
+}
+
+// Brick skip flags (and, with the derived bricks, the per-cell empty bits) under the
+// volume's current transfer function.
+vr_status classify_volume(vr_ctx* ctx, Volume* v) {
+    CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix, ctx->stream),
+       "classify");
+    if (v->d_cellmask)
+        CK(launch_classify_cells(v->d_cellq, v->nbricks, v->d_prefix, v->tp.tf_w, v->d_cellmask, ctx->stream),
+           "classify cells");
     return VR_OK;
 }
 
@@ -378,16 +397,35 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     if (v->d_dbricks && dbytes > ctx->derived_budget) {
         CK(cudaStreamSynchronize(ctx->stream), "precompute_morphology: sync");
         cudaFree(v->d_dbricks);
+        cudaFree(v->d_cellq);
+        cudaFree(v->d_cellmask);
         v->d_dbricks = nullptr;
+        v->d_cellq = nullptr;
+        v->d_cellmask = nullptr;
     }
     if (!v->d_dbricks && dbytes <= ctx->derived_budget) {
+        // derived bricks + per-cell min/max (4 B per cell) + per-cell empty bits
         cudaError_t e = dalloc(&v->d_dbricks, dbytes);
+        if (e == cudaSuccess) e = dalloc(&v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks);
+        if (e == cudaSuccess) e = dalloc(&v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            v->d_dbricks = nullptr;  // fall back to the per-sample stencils
+            cudaFree(v->d_dbricks);  // fall back to the per-sample stencils
+            cudaFree(v->d_cellq);
+            cudaFree(v->d_cellmask);
+            v->d_dbricks = nullptr;
+            v->d_cellq = nullptr;
+            v->d_cellmask = nullptr;
         }
     }
-    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    if (v->d_dbricks) {
+        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+        CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
+        if (v->params_ready) {
+            vr_status cs = classify_volume(ctx, v);
+            if (cs != VR_OK) return cs;
+        }
+    }
     if (n_sigmas > 0) {
         if (!v->d_vessel) {
             CK(dalloc(&v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
@@ -467,8 +505,8 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
         d.alpha_exp = tp->opacity_ref_step > 0.0f ? (float)((double)tp->step_vox * smin / (double)tp->opacity_ref_step)
                                                   : 0.0f;
     }
-    CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, tp->tf_w, tp->tf_h, v->d_empty, v->d_prefix, ctx->stream),
-       "classify");
+    vr_status cs = classify_volume(ctx, v);
+    if (cs != VR_OK) return cs;
     v->params_ready = true;
     return VR_OK;
 }
@@ -510,10 +548,7 @@ vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm) {
        "set_normalized copy");
     vr_status st = rebuild_bricks(ctx, v);
     if (st != VR_OK) return st;
-    if (v->params_ready)
-        CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix,
-                           ctx->stream),
-           "classify");
+    if (v->params_ready) return classify_volume(ctx, v);
     return VR_OK;
 }
 
@@ -584,10 +619,10 @@ vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma) {
        "prefilter: copy back");
     vr_status st = rebuild_bricks(ctx, v);
     if (st != VR_OK) return st;
-    if (v->params_ready)
-        CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix,
-                           ctx->stream),
-           "prefilter: classify");
+    if (v->params_ready) {
+        st = classify_volume(ctx, v);
+        if (st != VR_OK) return st;
+    }
     v->morph_ready = false;  // |grad I|max and vesselness describe the unfiltered volume
     return VR_OK;
 }
@@ -645,7 +680,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.counters = d_counters;
     L.ray_samples = d_ray_samples;
     L.ray_state = static_cast<float2*>(o.ray_state);
-    if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr;
+    if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr, L.vol.cellmask = nullptr;
     L.packet_w = o.packet_w;
     L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
     L.work_counter = ctx->d_work;

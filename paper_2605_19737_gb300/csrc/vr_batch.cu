@@ -16,7 +16,7 @@ namespace {
 template <bool kAllDerived>
 __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
     const int lane = threadIdx.x & 31;
-    unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0, shade_tot = 0;
+    unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0, shade_tot = 0, interp_tot = 0;
     while (true) {
         unsigned item = 0;
         if (lane == 0) item = atomicAdd(B.work_counter, 1u);
@@ -41,22 +41,23 @@ __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
         RayDev r;
         const bool hit = inside && setup_ray(vw.cam, vw.rc, i, j, v.n, v.s, r);
         float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        unsigned dense = 0, evald = 0, shaded = 0;
+        unsigned dense = 0, evald = 0, shaded = 0, interp = 0;
         if (hit) {
             if (kAllDerived || v.dbricks)
                 march_gather<true>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
-                                   dense, evald, shaded);
+                                   dense, evald, shaded, interp);
             else
                 march_gather<false>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
-                                    dense, evald, shaded);
+                                    dense, evald, shaded, interp);
         }
         if (inside) reinterpret_cast<float4*>(vw.out)[(long long)j * vw.W + i] = out;
         rays_hit += hit ? 1u : 0u;
         dense_tot += dense;
         eval_tot += evald;
         shade_tot += shaded;
+        interp_tot += interp;
     }
-    if (B.counters) add_counters(B.counters, rays_hit, dense_tot, eval_tot, 0u, shade_tot);
+    if (B.counters) add_counters(B.counters, rays_hit, dense_tot, eval_tot, 0u, shade_tot, interp_tot);
 }
 
 __global__ void __maxnreg__(72) k_render_batch_derived(const __grid_constant__ BatchLaunch B) { batch_body<true>(B); }

@@ -55,6 +55,8 @@ struct VolumeDev {
     const float* vbricks;    // vesselness bricks (same layout) or nullptr
     const float* dbricks;    // derived bricks or nullptr (then the per-sample stencils are used)
     const uint8_t* empty;    // nbricks flags, 1 = skip
+    const uint32_t* cellmask;  // with the derived bricks: nbricks x 16 words, bit (lz*8+ly)*8+lx set when
+                               // that cell is empty under the current transfer function; else nullptr
     const VolConst* vc;
 };
 
@@ -159,6 +161,10 @@ cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[
 cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], VolConst* vc, cudaStream_t st);
 cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
                             uint8_t* empty, int* prefix_scratch /* tf_w + 1 ints */, cudaStream_t st);
+constexpr int kCellsPerBrick = kCells * kCells * kCells;  // 512
+cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* cellq, cudaStream_t st);
+cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, const int* prefix, int tf_w,
+                                  uint32_t* cellmask, cudaStream_t st);
 
 // Multi-scale vesselness of `norm` into V (both nvox floats); tmp_a/tmp_b are
 // nvox-float scratch volumes, smax receives each scale's max Hessian norm.

@@ -17,18 +17,20 @@ __device__ __forceinline__ int brick_index(const VolumeDev& v, const int b[3]) {
 }
 
 __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, unsigned dense, unsigned evald,
-                                             unsigned staged, unsigned shaded) {
+                                             unsigned staged, unsigned shaded, unsigned interp) {
     const unsigned r = __reduce_add_sync(0xffffffffu, rays);
     const unsigned d = __reduce_add_sync(0xffffffffu, dense);
     const unsigned e = __reduce_add_sync(0xffffffffu, evald);
     const unsigned s = __reduce_add_sync(0xffffffffu, staged);
     const unsigned h = __reduce_add_sync(0xffffffffu, shaded);
+    const unsigned ip = __reduce_add_sync(0xffffffffu, interp);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&ctr->rays, (unsigned long long)r);
         atomicAdd(&ctr->dense_samples, (unsigned long long)d);
         atomicAdd(&ctr->evaluated_samples, (unsigned long long)e);
         atomicAdd(&ctr->bricks_staged, (unsigned long long)s);
         atomicAdd(&ctr->shaded_samples, (unsigned long long)h);
+        atomicAdd(&ctr->interpolated_samples, (unsigned long long)ip);
     }
 }
 
@@ -40,14 +42,14 @@ template <bool kDerived, bool kState = false, bool kParity = false>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
                                              float4& out, unsigned& dense, unsigned& evald, unsigned& shaded,
-                                             int* klast_out = nullptr, float* t_last = nullptr) {
+                                             unsigned& interp, int* klast_out = nullptr, float* t_last = nullptr) {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
     float A_prev = 0.f;  // kState: A before the last evaluated sample
     int klast = -1;      // kState: last evaluated sample
     int k1 = -1;         // kState: first sample with A >= 1 (where the adjoint sweep must start
     float T1 = 1.f;      // when early termination is off) and the transmittance in front of it
     int k = 0, kstop = -1;
-    unsigned ne = 0, nsh = 0;
+    unsigned ne = 0, nsh = 0, nip = 0;
     // The skip flag and the base pointers of the current brick are re-read only
     // when the brick changes (about every 16 samples), keeping a dependent L1 round
     // trip and the 64-bit address arithmetic off the path of every sample.
@@ -79,6 +81,17 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         }
         // local cell of (i0, j0, k0) within the brick: i0 - 8 bc = i0 & 7
         const int lx = i0[0] & 7, ly = i0[1] & 7, lz = i0[2] & 7;
+        if (kDerived && skip && v.cellmask) {
+            // a cell classified empty holds only samples of opacity exactly 0 (their
+            // intensity lies in the range of its 8 corners): nothing to read or add
+            const int c = (lz * kCells + ly) * kCells + lx;
+            if ((__ldg(v.cellmask + (size_t)bi * (kCellsPerBrick / 32) + (c >> 5)) >> (c & 31)) & 1u) {
+                ++ne;
+                ++k;
+                continue;
+            }
+        }
+        ++nip;
         const int base = (lz * kEdge + ly) * kEdge + lx;
         const float vval =
             v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
@@ -131,6 +144,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;
     evald = ne;
     shaded = nsh;
+    interp = nip;
     if (kState) {
         // the adjoint sweep starts at the first sample with A >= min(et, 1): the stopping
         // sample, or (early termination off) the first that made A reach 1

@@ -36,10 +36,12 @@ __global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const _
     RayDev r;
     const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
     float4 px = make_float4(0.f, 0.f, 0.f, 0.f);
-    unsigned dense = 0, evald = 0, shaded = 0;
+    unsigned dense = 0, evald = 0, shaded = 0, interp = 0;
     int kl = -1;
     float tl = 1.0f;
-    if (hit) march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, shaded, &kl, &tl);
+    if (hit)
+        march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, shaded, interp, &kl,
+                                       &tl);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         reinterpret_cast<float4*>(L.out)[pix] = px;
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const _
             L.ray_samples[2 * pix + 1] = evald;
         }
     }
-    if (L.counters) add_counters(L.counters, hit ? 1u : 0u, dense, evald, 0u, shaded);
+    if (L.counters) add_counters(L.counters, hit ? 1u : 0u, dense, evald, 0u, shaded, interp);
 }
 
 }  // namespace
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
         dense_tot += dense;
         eval_tot += evald;
     }
-    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u, eval_tot);
+    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u, eval_tot, eval_tot);
 }
 
 }  // namespace

@@ -282,7 +282,65 @@ __global__ void k_classify(const uint16_t* __restrict__ grid, long long nbricks,
     empty[b] = (uint8_t)(prefix[jh + 1] - prefix[jl] == 0);
 }
 
+// Per cell of each brick -- cell (lx, ly, lz) has corner voxels [8b + l, 8b + l + 1]
+// per axis -- the quantised min/max of I_norm over its 8 corners, with the brick
+// grid's rounding. Cells past the volume's last cell (corner index > N - 2) never
+// hold a sample and get the empty range (65535, 0). One CTA of 512 per brick.
+__global__ void __launch_bounds__(512) k_cell_minmax(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
+                                                     int nby, uint16_t* __restrict__ cellq) {
+    const long long b = blockIdx.x;
+    const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
+    const int c = threadIdx.x;
+    const int x = kCells * bx + (c & 7), y = kCells * by + ((c >> 3) & 7), z = kCells * bz + (c >> 6);
+    uint16_t ql = 65535, qh = 0;
+    if (x <= nx - 2 && y <= ny - 2 && z <= nz - 2) {
+        float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            acc(__ldg(norm + ((long long)(z + (q >> 2)) * ny + (y + ((q >> 1) & 1))) * nx + (x + (q & 1))), lo, hi);
+        ql = (uint16_t)fminf(fmaxf(floorf(__fmul_rn(lo, 65535.0f)), 0.0f), 65535.0f);
+        qh = (uint16_t)fminf(fmaxf(ceilf(__fmul_rn(hi, 65535.0f)), 0.0f), 65535.0f);
+    }
+    cellq[2 * (b * kCellsPerBrick + c)] = ql;
+    cellq[2 * (b * kCellsPerBrick + c) + 1] = qh;
+}
+
+// A cell is empty under the brick rule applied to its own range: no transfer-function
+// column in [floor(qlo*(w-1)/65535) - 1, ceil(qhi*(w-1)/65535) + 1] has any opacity
+// (every sample in the cell interpolates its 8 corners, so its intensity lies in the
+// range). Each warp packs the bits of 32 consecutive cells into one word.
+__global__ void __launch_bounds__(256) k_classify_cells(const uint16_t* __restrict__ cellq, long long ncells,
+                                                        const int* __restrict__ prefix, int w,
+                                                        uint32_t* __restrict__ cellmask) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // ncells is a multiple of 512
+    const long long ql = cellq[2 * e], qh = cellq[2 * e + 1];
+    bool empty = true;
+    if (ql <= qh) {
+        long long jl = (ql * (w - 1)) / 65535 - 1;
+        long long jh = (qh * (w - 1) + 65534) / 65535 + 1;
+        if (jl < 0) jl = 0;
+        if (jh > w - 1) jh = w - 1;
+        empty = prefix[jh + 1] - prefix[jl] == 0;
+    }
+    const unsigned bits = __ballot_sync(0xffffffffu, empty);
+    if ((threadIdx.x & 31) == 0) cellmask[e >> 5] = bits;
+    (void)ncells;
+}
+
 }  // namespace
+
+cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* cellq, cudaStream_t st) {
+    const long long nbr = (long long)nb[0] * nb[1] * nb[2];
+    k_cell_minmax<<<(unsigned)nbr, kCellsPerBrick, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], cellq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, const int* prefix, int tf_w,
+                                  uint32_t* cellmask, cudaStream_t st) {
+    const long long ncells = nbricks * kCellsPerBrick;
+    k_classify_cells<<<(unsigned)(ncells / 256), 256, 0, st>>>(cellq, ncells, prefix, tf_w, cellmask);
+    return cudaGetLastError();
+}
 
 int minmax_blocks(long long n) {
     long long want = (n + (long long)kReduceThreads * 16 - 1) / ((long long)kReduceThreads * 16);

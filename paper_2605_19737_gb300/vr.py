@@ -38,7 +38,7 @@ class vr_tissue_params(ctypes.Structure):
 class vr_counters(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_ulonglong), ("dense_samples", ctypes.c_ulonglong),
                 ("evaluated_samples", ctypes.c_ulonglong), ("bricks_staged", ctypes.c_ulonglong),
-                ("shaded_samples", ctypes.c_ulonglong)]
+                ("shaded_samples", ctypes.c_ulonglong), ("interpolated_samples", ctypes.c_ulonglong)]
 
 
 class vr_view(ctypes.Structure):

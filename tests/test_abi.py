@@ -48,7 +48,7 @@ def test_binding_matches_header(libpath):
 def test_struct_layouts():
     from paper_2605_19737_gb300 import vr
     assert ctypes.sizeof(vr.vr_camera) == 48
-    assert ctypes.sizeof(vr.vr_counters) == 40
+    assert ctypes.sizeof(vr.vr_counters) == 48
     assert ctypes.sizeof(vr.vr_render_opts) == 24
     # 3 ints, pointer (8-aligned), 3 ints, 10 floats -> 12 + 4 pad + 8 + 12 + 40 = 76 -> 80 (8-aligned)
     assert ctypes.sizeof(vr.vr_tissue_params) == 80

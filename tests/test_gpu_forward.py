@@ -256,30 +256,30 @@ def test_counters_match_ray_samples(vr, torch):
     assert c[1] == r[..., 0].sum() and c[2] == r[..., 1].sum()
     assert c[0] == int((r[..., 0] > 0).sum())
     assert c[3] > 0  # bricks staged into shared memory
-    assert c[4] == c[2]  # the stencil kernels shade every evaluated sample
+    assert c[4] == c[2] and c[5] == c[2]  # the stencil kernels interpolate and shade every evaluated sample
     vr.free_volume(vid)
 
 
 def test_shaded_samples_are_those_with_opacity(vr, torch):
-    """The derived-brick path computes the Hessian, Eq. 4 and the shading only for
-    samples whose transfer-function opacity is non-zero: fewer than the evaluated ones
-    under the Table 2 windows, all of them under an opacity that is nowhere zero --
-    and the images equal those of a path that shades every sample (the skipped ones
-    have alpha = 0 exactly)."""
+    """The derived-brick path skips cells classified empty and computes the Hessian,
+    Eq. 4 and the shading only for samples whose transfer-function opacity is non-zero:
+    shaded < interpolated < evaluated under the Table 2 windows, all equal under an
+    opacity that is nowhere zero. (That these skips change no pixel is
+    test_skip_is_bit_neutral_and_deterministic and the oracle parity.)"""
     import paper_2605_19737_gb300 as pkg
     case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
     vid = _load_case(vr, torch, case)
     ctr = pkg.new_counters()
     vr.render(vid, case["cams"], 64, 48, counters=ctr, kernel=1)
     c = ctr.cpu().numpy()
-    assert 0 < c[4] < c[2]
+    assert 0 < c[4] < c[5] < c[2]
     opaque = case["tf"].copy()
     opaque[..., 3] = np.maximum(opaque[..., 3], np.float32(0.01))
     vr.set_tissue_params(vid, opaque, **case["params"])
     ctr.zero_()
     vr.render(vid, case["cams"], 64, 48, counters=ctr, kernel=1)
     c = ctr.cpu().numpy()
-    assert c[4] == c[2]
+    assert c[4] == c[2] and c[5] == c[2]
     vr.free_volume(vid)
 
 
