@@ -152,6 +152,14 @@ def cpu_baseline(case, stride, threads=None):
             "seconds": dt, "dense_samples": dense}
 
 
+def workload_config(args, ws):
+    """The benchmark workload, as both arms report it."""
+    return {"workload": "brainweb_1080p", "volume": "181x217x181 u16 (BrainWeb-shaped phantom)",
+            "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows", "step_vox": 0.5,
+            "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def run_reference(args):
     from phantoms import workloads
     ws, rank, _ = _dist()
@@ -169,8 +177,7 @@ def run_reference(args):
     _json_line({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * last["seconds"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": "brainweb_1080p", "volume": "181x217x181 u16",
-                                                "image": "1920x1080", "sample": cb["sample"]},
+                "data": "synthetic", "config": dict(workload_config(args, 1), sample=cb["sample"]),
                 "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}})
 
@@ -455,7 +462,11 @@ def run(args):
     fp32_nominal = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     fma_ms, fma_flops = ctx.fma_peak()
     fp32_peak = fma_flops / 1e12
-    frame_flops = interp * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
+    # algorithmic: the method's per-sample arithmetic for every evaluated sample (the
+    # unit of the target design: samples outside empty bricks); executed: what the
+    # kernel ran after its exact skips (empty cells, zero-opacity samples)
+    frame_flops = evald * (FLOPS_STAGE1[kind] + FLOPS_SHADED[kind])
+    executed_flops = interp * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
     achieved_tflops = frame_flops / (ms * 1e-3) / 1e12
     if rank == 0:
         cb = None
@@ -466,17 +477,16 @@ def run(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "brainweb_1080p", "volume": "181x217x181 u16 (BrainWeb-shaped phantom)",
-                       "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows",
-                       "step_vox": 0.5, "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "config": workload_config(args, ws),
             "fps": 1000.0 / ms, "fps_wall": fps_wall,
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "interpolated_per_frame": interp,
                         "shaded_per_frame": shaded, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "flops_per_frame": frame_flops,
-                         "flops_per_sample": {"interpolated": FLOPS_STAGE1[kind], "shaded": FLOPS_SHADED[kind]},
+                         "flops_per_evaluated_sample": FLOPS_STAGE1[kind] + FLOPS_SHADED[kind],
+                         "algorithmic_flops_per_frame": frame_flops,
+                         "executed_flops_per_frame": executed_flops,
+                         "executed_tflops": executed_flops / (ms * 1e-3) / 1e12,
                          "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
                          "peak_source": "measured: FP32 FMA probe vr_fma_peak (8 independent chains per thread, "
                                         "%.3f ms per launch); nominal 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
