@@ -17,32 +17,25 @@ struct ParamGrad {
     float gamma, ka, kd, ks, os;
 };
 
-// Transfer-function gradient sink: a shared-memory table (1D; scalar shared
-// atomics) or a global one (one 16-byte vector atomic per RGBA entry). A lane's
-// consecutive samples mostly look up the same transfer-function cell, so the sink
-// accumulates the cell's (2 or 4) entry gradients in registers and writes them
-// out only when the cell changes (and once at the end of the ray: flush()).
+// Transfer-function gradient sink: one of the private global copies of the
+// gradient table, one 16-byte vector reduction per RGBA entry. (Shared-memory
+// tables with scalar atomics measured 1.6x slower on a 1D table: the lanes of a
+// CTA contend for the same few entries.) A lane's consecutive samples mostly look
+// up the same transfer-function cell, so the sink accumulates the cell's (2 or 4)
+// entry gradients in registers and writes them out only when the cell changes
+// (and once at the end of the ray: flush()).
 struct TfGradSink {
     float* p;
-    bool shared;
     int w;          // entries per row
     bool two_d;
     int key = -1;   // first entry of the pending cell, -1 = none
     float4 a00, a01, a10, a11;
 
-    __device__ __forceinline__ TfGradSink(float* p_, bool shared_, int w_, bool two_d_)
-        : p(p_), shared(shared_), w(w_), two_d(two_d_) {}
+    __device__ __forceinline__ TfGradSink(float* p_, int w_, bool two_d_) : p(p_), w(w_), two_d(two_d_) {}
 
     __device__ __forceinline__ void put(int entry, const float4& v) const {
-        if (shared) {
-            float* e = p + 4 * entry;
-            if (v.x != 0.0f) atomicAdd(e, v.x);
-            if (v.y != 0.0f) atomicAdd(e + 1, v.y);
-            if (v.z != 0.0f) atomicAdd(e + 2, v.z);
-            if (v.w != 0.0f) atomicAdd(e + 3, v.w);
-        } else if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f) {
+        if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f)
             atomicAdd(reinterpret_cast<float4*>(p) + entry, v);
-        }
     }
     __device__ __forceinline__ void flush() {
         if (key < 0) return;

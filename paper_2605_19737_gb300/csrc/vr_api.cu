@@ -769,8 +769,8 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     B.dtf = d_dtf;
     B.dparams = d_dparams;
     B.dvol = d_dvolume;
-    B.tf_in_smem = (v->tp.tf_h == 1 && ntf * sizeof(float) <= 64 * 1024) ? 1 : 0;
-    if (!B.tf_in_smem) {
+    {
+        // private copies of the transfer-function gradient, summed after the kernels
         const size_t need = sizeof(float) * ntf * kTfGradCopies;
         if (ctx->tfgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
@@ -797,9 +797,8 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (channels)
         CK(launch_channels_to_voxels(ctx->d_dgrad, v->n, v->s, d_dvolume, ctx->stream),
            "render_backward: channel gradients to voxels");
-    if (!B.tf_in_smem)
-        CK(launch_sum_copies(ctx->d_tfgrad, kTfGradCopies, (long long)ntf, d_dtf, ctx->stream),
-           "render_backward: sum gradient copies");
+    CK(launch_sum_copies(ctx->d_tfgrad, kTfGradCopies, (long long)ntf, d_dtf, ctx->stream),
+       "render_backward: sum gradient copies");
     return VR_OK;
 }
 

@@ -17,11 +17,10 @@
 //        dL/dc_k     = T_k alpha_k dL/dC              (Eqs. 5-6 differentiated);
 //   3. sample_adjoint / field_adjoint_scatter chain these to the parameters.
 // Transfer-function gradients are accumulated per lane while its samples stay in
-// one transfer-function cell; a 1D table is then summed in shared memory per CTA
-// and flushed with one atomic per non-zero entry; a 2D table is summed with
-// 16-byte vector atomics into 64 private global copies (CTA c into copy c % 64)
-// that k_sum_copies adds up afterwards -- contended atomics on one 256 KB table
-// cost 10x the rest of the kernel. Voxel gradients: on the derived bricks, per-
+// one transfer-function cell, then added with 16-byte vector atomics into 64
+// private global copies of the table (CTA c into copy c % 64) that k_sum_copies
+// adds up afterwards -- contended atomics on one 256 KB table cost 10x the rest
+// of the kernel, and a shared-memory table per CTA (1D tables) 1.6x the copies. Voxel gradients: on the derived bricks, per-
 // voxel channel gradients (vector atomics) and a gather pass through the stencil
 // transposes; otherwise scalar global atomics on the voxels. Uniform gradients are
 // warp-reduced first.
@@ -162,19 +161,12 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
 // the 3 that the unbounded register count allows.
 template <bool kDerived>
 __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
-    extern __shared__ float s_dtf[];
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
-    if (B.tf_in_smem) {
-        for (int e = threadIdx.x; e < ntf; e += blockDim.x) s_dtf[e] = 0.0f;
-        __syncthreads();
-    }
-    // 1D tables: one shared-memory copy per CTA. 2D tables (too large for shared
-    // memory): one of n_copies private global copies, so that CTAs working on the
-    // same hot entries do not serialise on one address.
+    // one of n_copies private global copies of the gradient table, so that CTAs
+    // working on the same hot entries do not serialise on one address
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    TfGradSink sink(tf_dst, B.tf_in_smem != 0, L.tp.tf_w, L.tp.tf_h > 1);
+    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ntf, L.tp.tf_w, L.tp.tf_h > 1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
     tile_pixel(L.packet_w, w, l, di, dj);
@@ -308,11 +300,6 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
         for (int e = 0; e < 5; ++e)
             if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
     }
-    if (B.tf_in_smem) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < ntf; e += blockDim.x)
-            if (s_dtf[e] != 0.0f) atomicAdd(B.dtf + e, s_dtf[e]);
-    }
 }
 
 // Brick-synchronous variant of the reverse sweep. Phase 1 (the forward
@@ -335,15 +322,11 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
     const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
-    float* s_dtf = smem;                                          // ntf floats when tf_in_smem
-    float* acc = smem + (B.tf_in_smem ? ((ntf + 31) & ~31) : 0) + warp * kBrickVox;  // this warp's 12^3 block
-    if (B.tf_in_smem)
-        for (int e = threadIdx.x; e < ntf; e += blockDim.x) s_dtf[e] = 0.0f;
+    float* acc = smem + warp * kBrickVox;  // this warp's 12^3 block
     for (int e = l; e < kBrickVox; e += 32) acc[e] = 0.0f;
     __syncthreads();
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    float* tf_dst = B.tf_in_smem ? s_dtf : B.dtf_copies + (size_t)(cta % B.n_copies) * ntf;
-    TfGradSink sink(tf_dst, B.tf_in_smem != 0, L.tp.tf_w, L.tp.tf_h > 1);
+    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ntf, L.tp.tf_w, L.tp.tf_h > 1);
     const int i = blockIdx.x * 16 + (warp & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (l >> 3);
     const int cam = blockIdx.z;
@@ -516,11 +499,6 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
         for (int e = 0; e < 5; ++e)
             if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
     }
-    if (B.tf_in_smem) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < ntf; e += blockDim.x)
-            if (s_dtf[e] != 0.0f) atomicAdd(B.dtf + e, s_dtf[e]);
-    }
 }
 
 // dtf[e] = sum of the n_copies private copies of entry e.
@@ -553,29 +531,18 @@ cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, fl
 cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st) {
     const RenderLaunch& L = B.r;
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
-    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
     if (staged) {
-        const int smem = (B.tf_in_smem ? ((ntf + 31) & ~31) * 4 : 0) + 4 * kBrickBytes;
+        const int smem = 4 * kBrickBytes;
         cudaError_t e = cudaFuncSetAttribute(k_render_backward_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             4 * kBrickBytes + 64 * 1024 + 128);
+                                             smem);
         if (e != cudaSuccess) return e;
         k_render_backward_staged<<<grid, 128, smem, st>>>(B);
         return cudaGetLastError();
     }
-    const int smem = B.tf_in_smem ? ntf * (int)sizeof(float) : 0;
-    if (smem > 48 * 1024 && !L.vol.dbricks) {
-        cudaError_t e = cudaFuncSetAttribute(k_render_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
-    if (L.vol.dbricks) {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_render_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-        }
-        k_render_backward<true><<<grid, 128, smem, st>>>(B);
-    } else {
-        k_render_backward<false><<<grid, 128, smem, st>>>(B);
-    }
+    if (L.vol.dbricks)
+        k_render_backward<true><<<grid, 128, 0, st>>>(B);
+    else
+        k_render_backward<false><<<grid, 128, 0, st>>>(B);
     return cudaGetLastError();
 }
 

@@ -112,8 +112,7 @@ struct BackwardLaunch {
     float* dtf;             // [tf_h][tf_w][4], zeroed by the caller
     float* dparams;         // gamma, ka, kd, ks, opacity_scale, zeroed by the caller
     float* dvol;            // nvox or nullptr, zeroed by the caller
-    int tf_in_smem;         // 1: sum 1D transfer-function gradients in shared memory first
-    float* dtf_copies;      // else: n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
+    float* dtf_copies;      // n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
     int n_copies;
     float* dgrad;           // derived-brick path with dvol: zeroed nvox x kDerFloats channel gradients, else nullptr
 };
