@@ -159,8 +159,18 @@ def test_opacity_correction_parity(vr, torch, step):
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
-def test_skip_is_bit_neutral_and_deterministic(vr, torch, kernel):
-    case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
+@pytest.mark.parametrize("which", ["brainweb_2d", "head_1d", "vessel"])
+def test_skip_is_bit_neutral_and_deterministic(vr, torch, kernel, which):
+    """Skipping empty bricks, empty cells (derived path) and zero-opacity samples
+    changes no bit of the image or of the per-ray sample counts."""
+    if which == "brainweb_2d":
+        case = workloads.scaled_brainweb((61, 73, 59), width=64, height=48, n_cams=2)
+    elif which == "head_1d":
+        case = dict(workloads.head64_128px(), W=64, H=48)
+        case["cams"] = ph.camera_array([ph.orbit_camera((64, 64, 64), (1, 1, 1), az, 15, width=64, height=48)
+                                        for az in (20, 200)])
+    else:
+        case = workloads.vessel_1080p(dims=(48, 40, 36), width=64, height=48)
     vid = _load_case(vr, torch, case)
     a, ra = _render(vr, torch, vid, case, skip_empty=True, kernel=kernel)
     b, rb = _render(vr, torch, vid, case, skip_empty=False, kernel=kernel)
