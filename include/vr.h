@@ -187,7 +187,10 @@ vr_status vr_nifti_info(const char* path, int* h_dims, float* h_spacing, int* h_
 vr_status vr_free_volume(vr_ctx* ctx, int vol_id);
 
 /* Per-volume morphology (Sec. 2.3 and Sec. 1), run once per volume:
- * |grad I|_max over voxels (Eq. 4's normaliser, a parallel reduction), and,
+ * |grad I|_max over voxels (Eq. 4's normaliser, a parallel reduction); the
+ * voxel-wise I, gradient and Hessian stored per brick for the raymarch (the
+ * "derived bricks", 12 floats per corner voxel, within the context's derived
+ * budget -- see vr_set_derived_budget) with each cell's quantised min/max; and,
  * when n_sigmas > 0, the multi-scale Frangi vesselness V = max over
  * h_sigmas[0..n_sigmas-1] (voxel units, each in (0, 8]) of the bright-vessel
  * response of the sigma^2-scaled Hessian of the Gaussian-smoothed volume,
@@ -196,7 +199,8 @@ vr_status vr_free_volume(vr_ctx* ctx, int vol_id);
 vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigmas, int n_sigmas);
 
 /* Set transfer-function and tissue uniforms (copied), then re-classify the
- * bricks for empty-space skipping. Nothing else is recomputed (the uniform
+ * bricks (and, with derived bricks, the cells) for empty-space skipping: two
+ * small kernels, tens of microseconds. Nothing else is recomputed (the uniform
  * buffers of the abstract and Sec. 4). Errors: INVALID_ARG (bad sizes or
  * values, 2D-vessel mode without vesselness), NOT_READY, OOM, CUDA. */
 vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* tp);
