@@ -98,7 +98,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -206,7 +206,7 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
     dvol = torch.empty(case["volume"].shape, device=dev)
     state = torch.empty((cams.shape[0], H, W, 2), device=dev)
     ts = []
-    for i in range(args.warmup + max(3, args.steps // 4)):
+    for i in range(args.warmup + max(3, min(20, args.steps // 4))):
         flush.zero_()
         s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         s0.record()
@@ -256,7 +256,7 @@ def run_batched(args, ctx, dev, flush):
     for _ in range(args.warmup):
         ctx.batch_render(bid, packet_w=pw, warps_per_block=wpb, graph=True)
     ts = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(max(3, min(10, args.steps // 2))):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
@@ -341,6 +341,7 @@ def run(args):
     if ws > 1:
         dist.barrier()
     clocks = Clocks(local)
+    time.sleep(0.3)  # let the sampler start before the timed region
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for s, e in evs:
@@ -404,7 +405,7 @@ def run(args):
         dvol = torch.empty(vol_np.shape, device=dev)
         state = torch.empty((1, H, W, 2), device=dev)
         fb = []
-        for i in range(args.warmup + max(3, args.steps // 4)):
+        for i in range(args.warmup + max(3, min(20, args.steps // 4))):
             flush.zero_()
             s0, s1, s2, s3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             s0.record()
@@ -514,7 +515,7 @@ def run(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
