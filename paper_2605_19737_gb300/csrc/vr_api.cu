@@ -67,7 +67,7 @@ struct vr_ctx {
     int partials_cap = 0;
     void* d_stage = nullptr;
     size_t stage_cap = 0;
-    float* d_scratch = nullptr;   // vesselness smoothing scratch (2 volumes)
+    float* d_scratch = nullptr;   // vesselness scratch (smoothed volume + 3 eigenvalue planes), prefilter
     size_t scratch_cap = 0;
     float* d_tfgrad = nullptr;    // private copies of a 2D transfer-function gradient
     size_t tfgrad_cap = 0;
@@ -432,7 +432,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
             CK(dalloc(&v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
             CK(dalloc(&v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
         }
-        const size_t need = sizeof(float) * 2 * (size_t)v->nvox;
+        const size_t need = sizeof(float) * 4 * (size_t)v->nvox;  // smoothed volume + 3 eigenvalue planes
         if (ctx->scratch_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "vesselness scratch sync");
             cudaFree(ctx->d_scratch);

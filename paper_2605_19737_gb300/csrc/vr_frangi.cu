@@ -110,8 +110,11 @@ __device__ __forceinline__ void eig3_sorted(const float H[6], float l[3]) {
     if (before(l[1], l[0])) { const float t = l[0]; l[0] = l[1]; l[1] = t; }
 }
 
-__global__ void __launch_bounds__(256) k_frangi_smax(const float* __restrict__ sm, int nx, int ny, int nz, float s2,
-                                                     float* __restrict__ smax) {
+// Per voxel: Hessian of the smoothed volume (x sigma^2), its eigenvalues sorted by
+// |lambda| (stored, one plane of the SoA `eig` per eigenvalue, for the second pass)
+// and the block maximum of S = |lambda|_2 folded into smax.
+__global__ void __launch_bounds__(256) k_frangi_eig(const float* __restrict__ sm, int nx, int ny, int nz, float s2,
+                                                    float* __restrict__ eig, float* __restrict__ smax) {
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     const int z = blockIdx.z;
@@ -121,6 +124,10 @@ __global__ void __launch_bounds__(256) k_frangi_smax(const float* __restrict__ s
         hessian_at(sm, nx, ny, nz, x, y, z, s2, H);
         eig3_sorted(H, l);
         S = sqrtf(fmaf(l[0], l[0], fmaf(l[1], l[1], l[2] * l[2])));
+        const long long nvox = (long long)nx * ny * nz, idx = ((long long)z * ny + y) * nx + x;
+        eig[idx] = l[0];
+        eig[nvox + idx] = l[1];
+        eig[2 * nvox + idx] = l[2];
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) S = fmaxf(S, __shfl_xor_sync(0xffffffffu, S, o));
@@ -133,15 +140,12 @@ __global__ void __launch_bounds__(256) k_frangi_smax(const float* __restrict__ s
     }
 }
 
-__global__ void __launch_bounds__(256) k_frangi_v(const float* __restrict__ sm, int nx, int ny, int nz, float s2,
+// Frangi response of this scale from the stored eigenvalues (c = smax / 2), max-combined into V.
+__global__ void __launch_bounds__(256) k_frangi_v(const float* __restrict__ eig, long long nvox,
                                                   const float* __restrict__ smax, float* __restrict__ V) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    const int z = blockIdx.z;
-    if (x >= nx || y >= ny) return;
-    float H[6], l[3];
-    hessian_at(sm, nx, ny, nz, x, y, z, s2, H);
-    eig3_sorted(H, l);
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nvox) return;
+    const float l[3] = {__ldg(eig + idx), __ldg(eig + nvox + idx), __ldg(eig + 2 * nvox + idx)};
     const float c = 0.5f * __ldg(smax);
     float v = 0.0f;
     if (!(l[1] > 0.0f || l[2] > 0.0f || l[1] == 0.0f || l[2] == 0.0f || c <= 0.0f)) {
@@ -151,7 +155,6 @@ __global__ void __launch_bounds__(256) k_frangi_v(const float* __restrict__ sm, 
         // alpha = beta = 0.5: 2 alpha^2 = 2 beta^2 = 0.5
         v = (1.0f - expf(-Ra * Ra / 0.5f)) * expf(-Rb * Rb / 0.5f) * (1.0f - expf(-S2 / (2.0f * c * c)));
     }
-    const long long idx = ((long long)z * ny + y) * nx + x;
     V[idx] = fmaxf(V[idx], v);
 }
 
@@ -172,7 +175,8 @@ cudaError_t launch_gauss3d(const float* in, float* out, float* tmp, const int n[
 }
 
 cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas, int n_sigmas, float* tmp_a,
-                          float* tmp_b, float* smax /* n_sigmas floats */, float* V, cudaStream_t st) {
+                          float* tmp_b /* 3 nvox floats */, float* smax /* n_sigmas floats */, float* V,
+                          cudaStream_t st) {
     const long long nvox = (long long)n[0] * n[1] * n[2];
     cudaError_t e = cudaMemsetAsync(V, 0, sizeof(float) * nvox, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(smax, 0, sizeof(float) * n_sigmas, st);
@@ -190,8 +194,9 @@ cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas
         k_gauss_axis<<<grid, 256, 0, st>>>(tmp_a, tmp_b, n[0], n[1], n[2], 1, G);
         k_gauss_axis<<<grid, 256, 0, st>>>(tmp_b, tmp_a, n[0], n[1], n[2], 2, G);
         const float s2 = (float)(sg * sg);
-        k_frangi_smax<<<grid, 256, 0, st>>>(tmp_a, n[0], n[1], n[2], s2, smax + si);
-        k_frangi_v<<<grid, 256, 0, st>>>(tmp_a, n[0], n[1], n[2], s2, smax + si, V);
+        // eigenvalues once (into tmp_b, free after the smoothing), then the response
+        k_frangi_eig<<<grid, 256, 0, st>>>(tmp_a, n[0], n[1], n[2], s2, tmp_b, smax + si);
+        k_frangi_v<<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(tmp_b, nvox, smax + si, V);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
