@@ -95,11 +95,15 @@ __device__ __forceinline__ void jacobi_rotate(float a[3][3], int p, int q) {
 // Eigenvalues sorted by |lambda| ascending (ties by lambda ascending).
 __device__ __forceinline__ void eig3_sorted(const float H[6], float l[3]) {
     float a[3][3] = {{H[0], H[3], H[4]}, {H[3], H[1], H[5]}, {H[4], H[5], H[2]}};
+    // cyclic sweeps until the off-diagonal part is below float resolution of the
+    // diagonal (quadratic convergence: 3-4 sweeps), at most 6
 #pragma unroll 1
     for (int sweep = 0; sweep < 6; ++sweep) {
         jacobi_rotate(a, 0, 1);
         jacobi_rotate(a, 0, 2);
         jacobi_rotate(a, 1, 2);
+        const float off = fabsf(a[0][1]) + fabsf(a[0][2]) + fabsf(a[1][2]);
+        if (off <= 1e-9f * (fabsf(a[0][0]) + fabsf(a[1][1]) + fabsf(a[2][2]))) break;
     }
     l[0] = a[0][0];
     l[1] = a[1][1];
