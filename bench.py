@@ -147,8 +147,9 @@ def cpu_baseline(case, stride, threads=None):
     dense = int(res.dense.sum())
     rays = len(range(0, case["H"], stride)) * len(range(0, case["W"], stride))
     return {"value": dense / dt / 1e9, "unit": UNIT, "cores": int(res.threads), "kind": "oracle",
-            "sample": "every %dth row and column of the 1920x1080 frame (%d rays, %d dense samples), "
-                      "including the oracle's voxel-derivative setup, %.1f s" % (stride, rays, dense, dt),
+            "sample": "every %dth row and column of the %dx%d frame (%d rays, %d dense samples), "
+                      "including the oracle's voxel-derivative setup, %.1f s" % (stride, case["W"], case["H"], rays,
+                                                                               dense, dt),
             "seconds": dt, "dense_samples": dense}
 
 
@@ -474,6 +475,10 @@ def run(args):
         if ws == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(workloads.brainweb_1080p(), stride=2)
             cb.pop("seconds", None)
+            # and the whole small head frame (64^3, 128x128, 1D TF), every pixel
+            small = cpu_baseline(workloads.head64_128px(), stride=1)
+            cb["head64_128px_full_frame"] = {"value": small["value"], "unit": UNIT,
+                                             "seconds": small["seconds"], "dense_samples": small["dense_samples"]}
         _json_line({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
