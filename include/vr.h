@@ -353,8 +353,9 @@ typedef struct {
  * The view table -- each volume's bricks, skip flags, transfer-function buffer
  * and uniforms at this moment, plus the cameras and outputs -- is uploaded once
  * to device memory (synchronises). Re-upload with vr_batch_update after
- * vr_set_tissue_params; vr_free_volume of a member volume invalidates the
- * batch. Errors: INVALID_ARG (unknown volume, bad size or output), NOT_READY
+ * vr_set_tissue_params, and after a vr_precompute_morphology that adds or drops
+ * a member volume's derived bricks (vr_set_derived_budget); vr_free_volume of a
+ * member volume invalidates the batch. Errors: INVALID_ARG (unknown volume, bad size or output), NOT_READY
  * (a volume without morphology or tissue params), OOM, CUDA. */
 vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* batch_id);
 vr_status vr_batch_update(vr_ctx* ctx, int batch_id);
