@@ -59,12 +59,16 @@ KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_
 
 
 def kernel_source_hash():
-    """sha256 over the sources of the forward raymarch kernel."""
+    """sha256 over the code (comments and blank lines removed) of the forward
+    raymarch kernel's sources."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = "\n".join(ln.split("//")[0].rstrip() for ln in code.splitlines())
+        h.update("\n".join(ln for ln in code.splitlines() if ln.strip()).encode())
     return h.hexdigest()[:16]
 
 
