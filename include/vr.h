@@ -105,7 +105,7 @@ typedef struct {
                                              nothing; all of them for the stencil kernels) */
     unsigned long long interpolated_samples; /* of the evaluated, those whose field was read:
                                              all but the ones in cells classified empty (the
-                                             derived-brick path skips those cells, bit-neutral) */
+                                             per-lane kernels skip those cells, bit-neutral) */
 } vr_counters;
 
 typedef enum {

@@ -34,7 +34,7 @@ struct Volume {
     float* d_vessel = nullptr;
     float* d_vbricks = nullptr;
     float* d_dbricks = nullptr;  // derived bricks (voxel-wise I, gradient, Hessian) or nullptr
-    uint16_t* d_cellq = nullptr;     // with the derived bricks: per-cell quantised min/max
+    uint16_t* d_cellq = nullptr;     // after the morphology precompute: per-cell quantised min/max
     uint32_t* d_cellmask = nullptr;  // and per-cell empty bits under the current transfer function
     float* d_smax = nullptr;  // per-scale max Hessian norm (8 floats)
     float* d_tf = nullptr;
@@ -186,15 +186,13 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
     CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
     CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
-    if (v->d_dbricks) {
-        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
-        CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
-    }
+    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    if (v->d_cellq) CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
     return VR_OK;
 }
 
-// Brick skip flags (and, with the derived bricks, the per-cell empty bits) under the
-// volume's current transfer function.
+// Brick skip flags and (once the morphology is precomputed) the per-cell empty bits
+// under the volume's current transfer function.
 vr_status classify_volume(vr_ctx* ctx, Volume* v) {
     CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix, ctx->stream),
        "classify");
@@ -397,34 +395,25 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     if (v->d_dbricks && dbytes > ctx->derived_budget) {
         CK(cudaStreamSynchronize(ctx->stream), "precompute_morphology: sync");
         cudaFree(v->d_dbricks);
-        cudaFree(v->d_cellq);
-        cudaFree(v->d_cellmask);
         v->d_dbricks = nullptr;
-        v->d_cellq = nullptr;
-        v->d_cellmask = nullptr;
     }
     if (!v->d_dbricks && dbytes <= ctx->derived_budget) {
-        // derived bricks + per-cell min/max (4 B per cell) + per-cell empty bits
         cudaError_t e = dalloc(&v->d_dbricks, dbytes);
-        if (e == cudaSuccess) e = dalloc(&v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks);
-        if (e == cudaSuccess) e = dalloc(&v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
-            cudaFree(v->d_dbricks);  // fall back to the per-sample stencils
-            cudaFree(v->d_cellq);
-            cudaFree(v->d_cellmask);
-            v->d_dbricks = nullptr;
-            v->d_cellq = nullptr;
-            v->d_cellmask = nullptr;
+            v->d_dbricks = nullptr;  // fall back to the per-sample stencils
         }
     }
-    if (v->d_dbricks) {
-        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
-        CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
-        if (v->params_ready) {
-            vr_status cs = classify_volume(ctx, v);
-            if (cs != VR_OK) return cs;
-        }
+    // per-cell min/max (4 B per cell) and per-cell empty bits, for either path
+    if (!v->d_cellq) {
+        CK(dalloc(&v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks), "cell grid");
+        CK(dalloc(&v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks), "cell flags");
+    }
+    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
+    if (v->params_ready) {
+        vr_status cs = classify_volume(ctx, v);
+        if (cs != VR_OK) return cs;
     }
     if (n_sigmas > 0) {
         if (!v->d_vessel) {
@@ -680,7 +669,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.counters = d_counters;
     L.ray_samples = d_ray_samples;
     L.ray_state = static_cast<float2*>(o.ray_state);
-    if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr, L.vol.cellmask = nullptr;
+    if (o.kernel == VR_KERNEL_GATHER_STENCIL) L.vol.dbricks = nullptr;
     L.packet_w = o.packet_w;
     L.packet_h = 32 / (o.packet_w > 0 ? o.packet_w : 8);
     L.work_counter = ctx->d_work;

@@ -55,8 +55,8 @@ struct VolumeDev {
     const float* vbricks;    // vesselness bricks (same layout) or nullptr
     const float* dbricks;    // derived bricks or nullptr (then the per-sample stencils are used)
     const uint8_t* empty;    // nbricks flags, 1 = skip
-    const uint32_t* cellmask;  // with the derived bricks: nbricks x 16 words, bit (lz*8+ly)*8+lx set when
-                               // that cell is empty under the current transfer function; else nullptr
+    const uint32_t* cellmask;  // nbricks x 16 words, bit (lz*8+ly)*8+lx set when that cell is empty
+                               // under the current transfer function (nullptr before the precompute)
     const VolConst* vc;
 };
 

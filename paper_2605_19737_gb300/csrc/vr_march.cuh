@@ -81,7 +81,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         }
         // local cell of (i0, j0, k0) within the brick: i0 - 8 bc = i0 & 7
         const int lx = i0[0] & 7, ly = i0[1] & 7, lz = i0[2] & 7;
-        if (kDerived && skip && v.cellmask) {
+        if (skip && v.cellmask) {
             // a cell classified empty holds only samples of opacity exactly 0 (their
             // intensity lies in the range of its 8 corners): nothing to read or add
             const int c = (lz * kCells + ly) * kCells + lx;
