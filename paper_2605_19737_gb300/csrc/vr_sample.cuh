@@ -88,12 +88,6 @@ __device__ __forceinline__ bool setup_ray(const CamDev& c, const RayConsts& rc, 
     return true;
 }
 
-// Continuous voxel coordinate of sample k along axis q (head + tail rounded to
-// one float; used where a rounding-level error only moves a brick decision).
-__device__ __forceinline__ float sample_u(const RayDev& r, int q, float kk) {
-    return fmaf(kk, r.dhi[q], r.uhi[q]) + fmaf(kk, r.dlo[q], r.ulo[q]);
-}
-
 // Cell of sample k along axis q: u_c = clamp(u, 0, n-1), i0 = min(floor(u_c), n-2),
 // f = u_c - i0. u = u_n + (k + 1/2) step is carried as a double-float (exact
 // product by FMA, exact sum by TwoSum) so that f is accurate to ~3e-8 at any
