@@ -386,6 +386,16 @@ vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts*
  * vr_precompute_morphology calls of this context. Errors: INVALID_ARG (NULL ctx). */
 vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes);
 
+/* Exercise the timeout path of the bounded device-side waits without faulting or
+ * hanging the GPU (the paper has no counterpart). Launches, on the context's
+ * stream, one CTA whose thread waits on an mbarrier phase that nothing completes,
+ * giving up after budget_cycles SM clocks (1..2^31; ~2^31 is about a second), and
+ * records the expired wait in the context's device status word exactly as a
+ * bulk copy that never landed would: the next vr_synchronize returns
+ * VR_ERR_TIMEOUT and clears the word, and the context stays usable.
+ * Errors: INVALID_ARG (budget out of range), CUDA. Asynchronous. */
+vr_status vr_probe_bounded_wait(vr_ctx* ctx, long long budget_cycles);
+
 /* Measure the device's FP32 FMA throughput (the paper has no counterpart; it is
  * the roof the raymarch's arithmetic is reported against, since the raymarch is
  * bound by the FP32 pipe and L1 rather than HBM). Launches, on the context's

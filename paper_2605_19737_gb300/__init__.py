@@ -268,6 +268,11 @@ class Context:
         0 = none (per-sample stencils)."""
         self._check(self._lib.vr_set_derived_budget(self._h, int(nbytes)))
 
+    def probe_bounded_wait(self, budget_cycles=1 << 20):
+        """Enqueue a bounded wait that expires; the next synchronize() raises VRError
+        with status VR_ERR_TIMEOUT (see vr_probe_bounded_wait)."""
+        self._check(self._lib.vr_probe_bounded_wait(self._h, int(budget_cycles)))
+
     def fma_peak(self, blocks=None, iters=2048, reps=5):
         """Measured FP32 FMA throughput: (median ms per launch, FLOP/s)."""
         if blocks is None:

@@ -1035,4 +1035,13 @@ vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes) {
     return VR_OK;
 }
 
+vr_status vr_probe_bounded_wait(vr_ctx* ctx, long long budget_cycles) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (budget_cycles < 1 || budget_cycles > (1LL << 31))
+        return fail(ctx, VR_ERR_INVALID_ARG, "probe_bounded_wait: budget outside [1, 2^31] cycles");
+    DeviceGuard g(ctx->device);
+    CK(launch_wait_probe(ctx->d_work + 1, budget_cycles, ctx->stream), "bounded-wait probe");
+    return VR_OK;
+}
+
 }  // extern "C"

@@ -184,6 +184,7 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
 // dtf[e] = sum over c of copies[c * n + e]
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t st);
+cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStream_t st);
 cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
                                       cudaStream_t st);
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,

@@ -4,6 +4,7 @@
 // Each thread runs 8 independent FMA chains, 16 steps unrolled per iteration, so
 // the FMA pipe, not its latency, limits the rate; the chains' results are stored
 // so that nothing is optimised away.
+#include "vr_async.cuh"
 #include "vr_internal.cuh"
 
 namespace vr {
@@ -28,7 +29,24 @@ __global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ out, int i
     out[tid] = s;
 }
 
+// One thread waits, with a clock budget, on an mbarrier phase that nothing will
+// complete (no arrivals, no transfers) -- the situation of a bulk copy that never
+// lands -- and records the expired wait in the status word as the raymarch does.
+__global__ void k_wait_probe(unsigned* __restrict__ status, long long budget) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(&bar, 0, budget)) atomicOr(status, kStatusTimeout);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(status, budget_cycles);
+    return cudaGetLastError();
+}
 
 // FLOPs of one launch: blocks * 256 threads * iters * 16 * 8 FMAs * 2.
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t st) {

@@ -19,3 +19,29 @@ def test_fma_peak_is_plausible():
         assert ms > 0.0 and 0.1 * nominal < flops <= nominal
         with pytest.raises(pkg.VRError):
             ctx.fma_peak(blocks=0)
+
+
+def test_expired_bounded_wait_is_reported_and_the_context_recovers():
+    """A device-side wait that nothing satisfies gives up after its clock budget; the
+    next synchronize reports VR_ERR_TIMEOUT once, and the context keeps rendering the
+    same image as before."""
+    torch = torch_cuda()
+    import numpy as np
+
+    import paper_2605_19737_gb300 as pkg
+    from phantoms import workloads
+    case = workloads.head64_128px()
+    with pkg.Context(0) as ctx:
+        vid = ctx.load_volume(torch.from_numpy(case["volume"]).cuda(), case["spacing"])
+        ctx.precompute_morphology(vid)
+        ctx.set_tissue_params(vid, case["tf"], **case["params"])
+        before = ctx.render(vid, case["cams"], case["W"], case["H"]).cpu().numpy()
+        ctx.probe_bounded_wait(1 << 20)  # ~0.5 ms of SM clocks
+        with pytest.raises(pkg.VRError) as e:
+            ctx.synchronize()
+        assert e.value.status == pkg.vr.VR_ERR_TIMEOUT
+        ctx.synchronize()  # reported once, then cleared
+        after = ctx.render(vid, case["cams"], case["W"], case["H"]).cpu().numpy()
+        np.testing.assert_array_equal(before, after)
+        with pytest.raises(pkg.VRError):
+            ctx.probe_bounded_wait(0)
