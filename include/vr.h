@@ -396,6 +396,32 @@ vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes);
  * Errors: INVALID_ARG (budget out of range), CUDA. Asynchronous. */
 vr_status vr_probe_bounded_wait(vr_ctx* ctx, long long budget_cycles);
 
+/* Device memory held by the context: every buffer the library allocates for it
+ * (volumes, derived bricks, cell grids, vesselness, batches, scratch) is counted
+ * in *bytes; caller-owned buffers (images, counters, ray state) are not. */
+vr_status vr_memory_used(vr_ctx* ctx, unsigned long long* bytes);
+
+/* Cap on vr_memory_used (0, the default: no cap beyond the device's memory). An
+ * allocation that would take the context past the cap fails as a cudaMalloc
+ * would: the call that needed it returns VR_ERR_OOM and releases nothing it did
+ * not allocate. Derived bricks are optional: a precompute that cannot get them
+ * under the cap renders from the per-sample stencils instead (same images within
+ * rounding). Lowering the cap below the current use frees nothing. */
+vr_status vr_set_memory_limit(vr_ctx* ctx, unsigned long long bytes);
+
+/* Fault injection for the out-of-memory paths (host side; nothing faults on the
+ * GPU): the next n_ok device allocations of the context succeed and the one
+ * after them fails as out of memory, once; n_ok = -1 cancels. *pending (may be
+ * NULL) receives the setting this call replaces: the allocations that were still
+ * to succeed before the injected failure, or -1 once it has happened (or when
+ * none was set). After a failed
+ * call the context and its other objects stay usable: a vr_load_volume that
+ * failed leaves no volume behind; a vr_precompute_morphology or
+ * vr_set_tissue_params that failed leaves the volume NOT_READY for rendering
+ * until the call is repeated successfully; a failed backward or batch call
+ * changes nothing. Errors: INVALID_ARG (n_ok < -1). */
+vr_status vr_debug_fail_alloc(vr_ctx* ctx, long long n_ok, long long* pending);
+
 /* Measure the device's FP32 FMA throughput (the paper has no counterpart; it is
  * the roof the raymarch's arithmetic is reported against, since the raymarch is
  * bound by the FP32 pipe and L1 rather than HBM). Launches, on the context's

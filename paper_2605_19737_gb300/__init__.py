@@ -268,6 +268,24 @@ class Context:
         0 = none (per-sample stencils)."""
         self._check(self._lib.vr_set_derived_budget(self._h, int(nbytes)))
 
+    def memory_used(self):
+        """Device bytes the library holds for this context (see vr_memory_used)."""
+        out = ctypes.c_ulonglong()
+        self._check(self._lib.vr_memory_used(self._h, ctypes.byref(out)))
+        return out.value
+
+    def set_memory_limit(self, nbytes):
+        """Cap on memory_used(); 0 = none. Allocations past it raise VRError(VR_ERR_OOM)."""
+        self._check(self._lib.vr_set_memory_limit(self._h, int(nbytes)))
+
+    def debug_fail_alloc(self, n_ok):
+        """Let n_ok more device allocations succeed and fail the next one as out of
+        memory (once); -1 cancels. Returns the replaced setting: allocations still to
+        succeed before the injected failure, or -1 once it has happened."""
+        pending = ctypes.c_longlong()
+        self._check(self._lib.vr_debug_fail_alloc(self._h, int(n_ok), ctypes.byref(pending)))
+        return pending.value
+
     def probe_bounded_wait(self, budget_cycles=1 << 20):
         """Enqueue a bounded wait that expires; the next synchronize() raises VRError
         with status VR_ERR_TIMEOUT (see vr_probe_bounded_wait)."""

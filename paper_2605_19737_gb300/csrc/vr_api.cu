@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -81,6 +82,10 @@ struct vr_ctx {
     int next_batch = 1;
     cudaStream_t graph_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::unordered_map<void*, size_t> allocs;  // device buffers held, with their sizes
+    size_t mem_used = 0;                       // sum of allocs
+    size_t mem_limit = 0;                      // 0: no limit beyond the device's
+    long long fail_after = -1;                 // >= 0: allocations left before an injected failure
 };
 
 namespace {
@@ -110,26 +115,54 @@ vr_status cuda_fail(vr_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
     } while (0)
 
+// Every device buffer of a context is allocated and freed here, so that the context
+// knows what it holds (vr_memory_used), can refuse to grow past a limit
+// (vr_set_memory_limit) and can be made to see an allocation fail (vr_debug_fail_alloc).
+// A refused allocation returns cudaErrorMemoryAllocation like a failed cudaMalloc.
 template <class T>
-cudaError_t dalloc(T** p, size_t bytes) {
-    return cudaMalloc((void**)p, bytes);
+cudaError_t dalloc(vr_ctx* ctx, T** p, size_t bytes) {
+    *p = nullptr;
+    if (ctx->fail_after == 0) {
+        ctx->fail_after = -1;  // one injected failure, then allocation behaves normally
+        return cudaErrorMemoryAllocation;
+    }
+    if (ctx->fail_after > 0) --ctx->fail_after;
+    if (ctx->mem_limit && bytes > ctx->mem_limit - std::min(ctx->mem_limit, ctx->mem_used))
+        return cudaErrorMemoryAllocation;
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return e;
+    ctx->allocs[q] = bytes;
+    ctx->mem_used += bytes;
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
 }
 
-void free_volume(Volume* v) {
-    cudaFree(v->d_norm);
-    cudaFree(v->d_bricks);
-    cudaFree(v->d_grid);
-    cudaFree(v->d_empty);
-    cudaFree(v->d_vc);
-    cudaFree(v->d_minmax);
-    cudaFree(v->d_vessel);
-    cudaFree(v->d_vbricks);
-    cudaFree(v->d_dbricks);
-    cudaFree(v->d_cellq);
-    cudaFree(v->d_cellmask);
-    cudaFree(v->d_smax);
-    cudaFree(v->d_tf);
-    cudaFree(v->d_prefix);
+void dfree(vr_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = ctx->allocs.find(p);
+    if (it != ctx->allocs.end()) {
+        ctx->mem_used -= it->second;
+        ctx->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+void free_volume(vr_ctx* ctx, Volume* v) {
+    dfree(ctx, v->d_norm);
+    dfree(ctx, v->d_bricks);
+    dfree(ctx, v->d_grid);
+    dfree(ctx, v->d_empty);
+    dfree(ctx, v->d_vc);
+    dfree(ctx, v->d_minmax);
+    dfree(ctx, v->d_vessel);
+    dfree(ctx, v->d_vbricks);
+    dfree(ctx, v->d_dbricks);
+    dfree(ctx, v->d_cellq);
+    dfree(ctx, v->d_cellmask);
+    dfree(ctx, v->d_smax);
+    dfree(ctx, v->d_tf);
+    dfree(ctx, v->d_prefix);
     delete v;
 }
 
@@ -142,10 +175,10 @@ cudaError_t ensure_stage(vr_ctx* ctx, size_t bytes) {
     if (ctx->stage_cap >= bytes) return cudaSuccess;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return e;
-    cudaFree(ctx->d_stage);
+    dfree(ctx, ctx->d_stage);
     ctx->d_stage = nullptr;
     ctx->stage_cap = 0;
-    e = cudaMalloc(&ctx->d_stage, bytes);
+    e = dalloc(ctx, &ctx->d_stage, bytes);
     if (e == cudaSuccess) ctx->stage_cap = bytes;
     return e;
 }
@@ -226,9 +259,10 @@ vr_status vr_create(vr_ctx** out, int device, void* cuda_stream) {
     ctx->device = device;
     ctx->stream = (cudaStream_t)cuda_stream;
     DeviceGuard g(device);
-    cudaError_t e = cudaMalloc(&ctx->d_work, 64 * sizeof(unsigned));
+    cudaError_t e = dalloc(ctx, &ctx->d_work, 64 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_work, 0, 64 * sizeof(unsigned));
     if (e != cudaSuccess) {
+        dfree(ctx, ctx->d_work);
         delete ctx;
         (void)cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
@@ -243,20 +277,20 @@ vr_status vr_destroy(vr_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& kv : ctx->batches) {
         for (auto& g : kv.second->graphs) cudaGraphExecDestroy(g.second);
-        cudaFree(kv.second->d_views);
-        cudaFree(kv.second->d_prefix);
+        dfree(ctx, kv.second->d_views);
+        dfree(ctx, kv.second->d_prefix);
         delete kv.second;
     }
-    for (auto& kv : ctx->vols) free_volume(kv.second);
+    for (auto& kv : ctx->vols) free_volume(ctx, kv.second);
     if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
-    cudaFree(ctx->d_partials);
-    cudaFree(ctx->d_stage);
-    cudaFree(ctx->d_scratch);
-    cudaFree(ctx->d_tfgrad);
-    cudaFree(ctx->d_dgrad);
-    cudaFree(ctx->d_work);
+    dfree(ctx, ctx->d_partials);
+    dfree(ctx, ctx->d_stage);
+    dfree(ctx, ctx->d_scratch);
+    dfree(ctx, ctx->d_tfgrad);
+    dfree(ctx, ctx->d_dgrad);
+    dfree(ctx, ctx->d_work);
     (void)cudaGetLastError();
     delete ctx;
     return VR_OK;
@@ -293,10 +327,10 @@ vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long
     const int nblocks = minmax_blocks(n);
     if (ctx->partials_cap < nblocks) {
         CK(cudaStreamSynchronize(ctx->stream), "reduce_minmax sync");
-        cudaFree(ctx->d_partials);
+        dfree(ctx, ctx->d_partials);
         ctx->d_partials = nullptr;
         ctx->partials_cap = 0;
-        CK(dalloc(&ctx->d_partials, sizeof(float) * 2 * nblocks), "reduce_minmax scratch");
+        CK(dalloc(ctx, &ctx->d_partials, sizeof(float) * 2 * nblocks), "reduce_minmax scratch");
         ctx->partials_cap = nblocks;
     }
     CK(launch_minmax_partials(d_data, dtype, n, ctx->d_partials, nblocks, ctx->stream), "minmax partials");
@@ -322,12 +356,12 @@ vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype 
     v->nbricks = (long long)v->nb[0] * v->nb[1] * v->nb[2];
     const size_t esz = dtype == VR_F32 ? 4 : 2;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dalloc(&v->d_norm, sizeof(float) * v->nvox);
-    if (e == cudaSuccess) e = dalloc(&v->d_bricks, (size_t)kBrickBytes * v->nbricks);
-    if (e == cudaSuccess) e = dalloc(&v->d_grid, sizeof(uint16_t) * 2 * v->nbricks);
-    if (e == cudaSuccess) e = dalloc(&v->d_empty, v->nbricks);
-    if (e == cudaSuccess) e = dalloc(&v->d_vc, sizeof(VolConst));
-    if (e == cudaSuccess) e = dalloc(&v->d_minmax, 2 * sizeof(float));
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_norm, sizeof(float) * v->nvox);
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_bricks, (size_t)kBrickBytes * v->nbricks);
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_grid, sizeof(uint16_t) * 2 * v->nbricks);
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_empty, v->nbricks);
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_vc, sizeof(VolConst));
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_minmax, 2 * sizeof(float));
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_vc, 0, sizeof(VolConst), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_empty, 0, v->nbricks, ctx->stream);
     const void* raw = data;
@@ -337,7 +371,7 @@ vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype 
         raw = ctx->d_stage;
     }
     if (e != cudaSuccess) {
-        free_volume(v);
+        free_volume(ctx, v);
         return cuda_fail(ctx, e, "load_volume: allocate/copy");
     }
     vr_status st = vr_reduce_minmax(ctx, raw, dtype, v->nvox, v->d_minmax);
@@ -359,7 +393,7 @@ vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype 
         st = fail(ctx, VR_ERR_INVALID_ARG, "load_volume: non-finite intensities");
     if (st != VR_OK) {
         cudaStreamSynchronize(ctx->stream);
-        free_volume(v);
+        free_volume(ctx, v);
         return st;
     }
     const int id = ctx->next_id++;
@@ -374,7 +408,7 @@ vr_status vr_free_volume(vr_ctx* ctx, int vol_id) {
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "free_volume: unknown id %d", vol_id);
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    free_volume(v);
+    free_volume(ctx, v);
     ctx->vols.erase(vol_id);
     return VR_OK;
 }
@@ -389,26 +423,27 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         if (!(h_sigmas[i] > 0.0f && h_sigmas[i] <= 8.0f))
             return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: sigma %g outside (0, 8]", (double)h_sigmas[i]);
     DeviceGuard g(ctx->device);
+    v->morph_ready = false;  // until every step below has been issued
     CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
     // voxel-wise derivatives for the raymarch (Sec. 2.3), within a memory budget
     const size_t dbytes = sizeof(float) * (size_t)kDerBrickFloats * v->nbricks;
     if (v->d_dbricks && dbytes > ctx->derived_budget) {
         CK(cudaStreamSynchronize(ctx->stream), "precompute_morphology: sync");
-        cudaFree(v->d_dbricks);
+        dfree(ctx, v->d_dbricks);
         v->d_dbricks = nullptr;
     }
     if (!v->d_dbricks && dbytes <= ctx->derived_budget) {
-        cudaError_t e = dalloc(&v->d_dbricks, dbytes);
+        cudaError_t e = dalloc(ctx, &v->d_dbricks, dbytes);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
             v->d_dbricks = nullptr;  // fall back to the per-sample stencils
         }
     }
     // per-cell min/max (4 B per cell) and per-cell empty bits, for either path
-    if (!v->d_cellq) {
-        CK(dalloc(&v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks), "cell grid");
-        CK(dalloc(&v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks), "cell flags");
-    }
+    if (!v->d_cellq)
+        CK(dalloc(ctx, &v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks), "cell grid");
+    if (!v->d_cellmask)
+        CK(dalloc(ctx, &v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks), "cell flags");
     if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
     CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
     if (v->params_ready) {
@@ -416,18 +451,16 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         if (cs != VR_OK) return cs;
     }
     if (n_sigmas > 0) {
-        if (!v->d_vessel) {
-            CK(dalloc(&v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
-            CK(dalloc(&v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
-            CK(dalloc(&v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
-        }
+        if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
+        if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
+        if (!v->d_smax) CK(dalloc(ctx, &v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
         const size_t need = sizeof(float) * 4 * (size_t)v->nvox;  // smoothed volume + 3 eigenvalue planes
         if (ctx->scratch_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "vesselness scratch sync");
-            cudaFree(ctx->d_scratch);
+            dfree(ctx, ctx->d_scratch);
             ctx->d_scratch = nullptr;
             ctx->scratch_cap = 0;
-            CK(dalloc(&ctx->d_scratch, need), "vesselness scratch");
+            CK(dalloc(ctx, &ctx->d_scratch, need), "vesselness scratch");
             ctx->scratch_cap = need;
         }
         CK(launch_frangi(v->d_norm, v->n, h_sigmas, n_sigmas, ctx->d_scratch, ctx->d_scratch + v->nvox, v->d_smax,
@@ -461,21 +494,22 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
     if ((tp->grad_mod != 0 && tp->grad_mod != 1) || (tp->shading != 0 && tp->shading != 1))
         return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: grad_mod/shading must be 0 or 1");
     DeviceGuard g(ctx->device);
+    v->params_ready = false;  // until the table is uploaded and the volume re-classified
     const size_t bytes = sizeof(float) * 4 * (size_t)tp->tf_w * tp->tf_h;
     if (v->tf_cap < bytes) {
         CK(cudaStreamSynchronize(ctx->stream), "set_tissue_params sync");
-        cudaFree(v->d_tf);
+        dfree(ctx, v->d_tf);
         v->d_tf = nullptr;
         v->tf_cap = 0;
-        CK(dalloc(&v->d_tf, bytes), "transfer function");
+        CK(dalloc(ctx, &v->d_tf, bytes), "transfer function");
         v->tf_cap = bytes;
     }
     if (v->prefix_cap < tp->tf_w + 1) {
         CK(cudaStreamSynchronize(ctx->stream), "set_tissue_params sync");
-        cudaFree(v->d_prefix);
+        dfree(ctx, v->d_prefix);
         v->d_prefix = nullptr;
         v->prefix_cap = 0;
-        CK(dalloc(&v->d_prefix, sizeof(int) * (tp->tf_w + 1)), "classification scratch");
+        CK(dalloc(ctx, &v->d_prefix, sizeof(int) * (tp->tf_w + 1)), "classification scratch");
         v->prefix_cap = tp->tf_w + 1;
     }
     CK(cudaMemcpyAsync(v->d_tf, tp->tf, bytes, tp->tf_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -592,10 +626,10 @@ vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma) {
     const size_t need = sizeof(float) * 2 * (size_t)v->nvox;
     if (ctx->scratch_cap < need) {
         CK(cudaStreamSynchronize(ctx->stream), "prefilter: scratch sync");
-        cudaFree(ctx->d_scratch);
+        dfree(ctx, ctx->d_scratch);
         ctx->d_scratch = nullptr;
         ctx->scratch_cap = 0;
-        CK(dalloc(&ctx->d_scratch, need), "prefilter: scratch");
+        CK(dalloc(ctx, &ctx->d_scratch, need), "prefilter: scratch");
         ctx->scratch_cap = need;
     }
     float* a = ctx->d_scratch;
@@ -743,10 +777,10 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         const size_t need = sizeof(float) * kDerFloats * (size_t)v->nvox;
         if (ctx->dgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
-            cudaFree(ctx->d_dgrad);
+            dfree(ctx, ctx->d_dgrad);
             ctx->d_dgrad = nullptr;
             ctx->dgrad_cap = 0;
-            CK(dalloc(&ctx->d_dgrad, need), "render_backward: channel gradient scratch");
+            CK(dalloc(ctx, &ctx->d_dgrad, need), "render_backward: channel gradient scratch");
             ctx->dgrad_cap = need;
         }
         CK(cudaMemsetAsync(ctx->d_dgrad, 0, need, ctx->stream), "render_backward: zero channel gradients");
@@ -763,10 +797,10 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         const size_t need = sizeof(float) * ntf * kTfGradCopies;
         if (ctx->tfgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
-            cudaFree(ctx->d_tfgrad);
+            dfree(ctx, ctx->d_tfgrad);
             ctx->d_tfgrad = nullptr;
             ctx->tfgrad_cap = 0;
-            CK(dalloc(&ctx->d_tfgrad, need), "render_backward: transfer-function gradient scratch");
+            CK(dalloc(ctx, &ctx->d_tfgrad, need), "render_backward: transfer-function gradient scratch");
             ctx->tfgrad_cap = need;
         }
         CK(cudaMemsetAsync(ctx->d_tfgrad, 0, need, ctx->stream), "render_backward: zero scratch");
@@ -897,17 +931,17 @@ vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* b
     DeviceGuard g(ctx->device);
     Batch* b = new Batch();
     b->views.assign(views, views + n_views);
-    cudaError_t e = dalloc(&b->d_views, sizeof(ViewDev) * n_views);
-    if (e == cudaSuccess) e = dalloc(&b->d_prefix, sizeof(int) * 4 * n_views);
+    cudaError_t e = dalloc(ctx, &b->d_views, sizeof(ViewDev) * n_views);
+    if (e == cudaSuccess) e = dalloc(ctx, &b->d_prefix, sizeof(int) * 4 * n_views);
     if (e != cudaSuccess) {
-        cudaFree(b->d_views);
+        dfree(ctx, b->d_views);
         delete b;
         return cuda_fail(ctx, e, "batch_create: allocate");
     }
     vr_status st = batch_upload(ctx, b);
     if (st != VR_OK) {
-        cudaFree(b->d_views);
-        cudaFree(b->d_prefix);
+        dfree(ctx, b->d_views);
+        dfree(ctx, b->d_prefix);
         delete b;
         return st;
     }
@@ -988,8 +1022,8 @@ vr_status vr_batch_free(vr_ctx* ctx, int batch_id) {
     cudaStreamSynchronize(ctx->stream);
     if (ctx->graph_stream) cudaStreamSynchronize(ctx->graph_stream);
     for (auto& gx : it->second->graphs) cudaGraphExecDestroy(gx.second);
-    cudaFree(it->second->d_views);
-    cudaFree(it->second->d_prefix);
+    dfree(ctx, it->second->d_views);
+    dfree(ctx, it->second->d_prefix);
     delete it->second;
     ctx->batches.erase(it);
     return VR_OK;
@@ -1002,7 +1036,7 @@ vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms,
         return fail(ctx, VR_ERR_INVALID_ARG, "fma_peak: bad arguments");
     DeviceGuard g(ctx->device);
     float* out = nullptr;
-    CK(dalloc(&out, sizeof(float) * 256 * (size_t)blocks), "fma_peak scratch");
+    CK(dalloc(ctx, &out, sizeof(float) * 256 * (size_t)blocks), "fma_peak scratch");
     cudaEvent_t ev[2 * 64 + 2];
     int made = 0;
     cudaError_t e = cudaSuccess;
@@ -1021,7 +1055,7 @@ vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms,
         ms.push_back(t);
     }
     for (int q = 0; q < made; ++q) cudaEventDestroy(ev[q]);
-    cudaFree(out);
+    dfree(ctx, out);
     if (e != cudaSuccess) return fail(ctx, VR_ERR_CUDA, "fma_peak: %s", cudaGetErrorString(e));
     std::sort(ms.begin(), ms.end());
     *h_ms = ms[ms.size() / 2];
@@ -1032,6 +1066,27 @@ vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms,
 vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes) {
     if (!ctx) return VR_ERR_INVALID_ARG;
     ctx->derived_budget = (size_t)bytes;
+    return VR_OK;
+}
+
+vr_status vr_set_memory_limit(vr_ctx* ctx, unsigned long long bytes) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    ctx->mem_limit = (size_t)bytes;
+    return VR_OK;
+}
+
+vr_status vr_memory_used(vr_ctx* ctx, unsigned long long* bytes) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (!bytes) return fail(ctx, VR_ERR_INVALID_ARG, "memory_used: NULL pointer");
+    *bytes = (unsigned long long)ctx->mem_used;
+    return VR_OK;
+}
+
+vr_status vr_debug_fail_alloc(vr_ctx* ctx, long long n_ok, long long* pending) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    if (n_ok < -1) return fail(ctx, VR_ERR_INVALID_ARG, "debug_fail_alloc: n_ok must be >= -1");
+    if (pending) *pending = ctx->fail_after;
+    ctx->fail_after = n_ok;
     return VR_OK;
 }
 

@@ -83,6 +83,9 @@ SIGNATURES = {
     "vr_classify_bricks_noalloc": ([_P, _LL, _P, _I, _I, _P, _P, ctypes.c_char_p, _I], _I),
     "vr_set_derived_budget": ([_P, ctypes.c_ulonglong], _I),
     "vr_probe_bounded_wait": ([_P, _LL], _I),
+    "vr_memory_used": ([_P, ctypes.POINTER(ctypes.c_ulonglong)], _I),
+    "vr_set_memory_limit": ([_P, ctypes.c_ulonglong], _I),
+    "vr_debug_fail_alloc": ([_P, _LL, ctypes.POINTER(_LL)], _I),
     "vr_fma_peak": ([_P, _I, _I, _I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double)], _I),
     "vr_batch_create": ([_P, _P, _I, ctypes.POINTER(_I)], _I),
     "vr_batch_update": ([_P, _I], _I),

@@ -247,6 +247,6 @@ def test_autograd_and_short_fit(vr, torch):
         lo = ((img - target) ** 2).mean()
         lo.backward()
         opt.step()
-        losses.append(float(lo))
+        losses.append(float(lo.detach()))
     assert losses[-1] < 0.5 * losses[0], losses
     vr.free_volume(vid)
