@@ -14,6 +14,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vr_async.cuh"
 #include "vr_internal.cuh"
 
@@ -183,6 +185,15 @@ cudaError_t ensure_stage(vr_ctx* ctx, size_t bytes) {
     return e;
 }
 
+// An NVTX range around each public call that enqueues GPU work, so that a trace
+// (Nsight Systems or Compute) shows which library call launched each kernel.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -340,6 +351,7 @@ vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long
 
 vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype dtype, int nx, int ny, int nz,
                          float sx, float sy, float sz, int* vol_id) {
+    NvtxRange range_("vr_load_volume");
     if (!ctx) return VR_ERR_INVALID_ARG;
     if (!data || !vol_id) return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: NULL pointer");
     if (dtype != VR_F32 && dtype != VR_U16) return fail(ctx, VR_ERR_INVALID_ARG, "load_volume: bad dtype");
@@ -414,6 +426,7 @@ vr_status vr_free_volume(vr_ctx* ctx, int vol_id) {
 }
 
 vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigmas, int n_sigmas) {
+    NvtxRange range_("vr_precompute_morphology");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "precompute_morphology: unknown id %d", vol_id);
@@ -473,6 +486,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
 }
 
 vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* tp) {
+    NvtxRange range_("vr_set_tissue_params");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: unknown id %d", vol_id);
@@ -563,6 +577,7 @@ vr_status vr_set_gmax(vr_ctx* ctx, int vol_id, float gmax) {
 }
 
 vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm) {
+    NvtxRange range_("vr_set_normalized");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v || !d_norm) return fail(ctx, VR_ERR_INVALID_ARG, "set_normalized: bad arguments");
@@ -616,6 +631,7 @@ vr_status vr_get_normalized(vr_ctx* ctx, int vol_id, float* out, int out_on_devi
 }
 
 vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma) {
+    NvtxRange range_("vr_prefilter");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "prefilter: unknown id %d", vol_id);
@@ -652,6 +668,7 @@ vr_status vr_prefilter(vr_ctx* ctx, int vol_id, int mode, float sigma) {
 
 vr_status vr_tissue_histogram(vr_ctx* ctx, int vol_id, int lo_bin, int hi_bin, unsigned long long* d_hist,
                               int* d_peaks) {
+    NvtxRange range_("vr_tissue_histogram");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "tissue_histogram: unknown id %d", vol_id);
@@ -667,6 +684,7 @@ vr_status vr_tissue_histogram(vr_ctx* ctx, int vol_id, int lo_bin, int hi_bin, u
 vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H, float* out_rgba,
                     int out_on_host, const vr_render_opts* opts, vr_counters* d_counters,
                     unsigned int* d_ray_samples) {
+    NvtxRange range_("vr_render");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "render: unknown id %d", vol_id);
@@ -742,6 +760,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
 vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams, int W, int H,
                              const float* d_dl_drgba, float* d_dtf, float* d_dparams, float* d_dvolume,
                              const vr_render_opts* opts) {
+    NvtxRange range_("vr_render_backward");
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: unknown id %d", vol_id);
@@ -918,6 +937,7 @@ vr_status batch_opts(vr_ctx* ctx, const vr_render_opts* opts, vr_render_opts* o)
 }  // namespace
 
 vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* batch_id) {
+    NvtxRange range_("vr_batch_create");
     if (!ctx) return VR_ERR_INVALID_ARG;
     if (!views || !batch_id || n_views < 1 || n_views > (1 << 20))
         return fail(ctx, VR_ERR_INVALID_ARG, "batch_create: bad arguments");
@@ -952,6 +972,7 @@ vr_status vr_batch_create(vr_ctx* ctx, const vr_view* views, int n_views, int* b
 }
 
 vr_status vr_batch_update(vr_ctx* ctx, int batch_id) {
+    NvtxRange range_("vr_batch_update");
     if (!ctx) return VR_ERR_INVALID_ARG;
     auto it = ctx->batches.find(batch_id);
     if (it == ctx->batches.end()) return fail(ctx, VR_ERR_INVALID_ARG, "batch_update: unknown batch %d", batch_id);
@@ -960,6 +981,7 @@ vr_status vr_batch_update(vr_ctx* ctx, int batch_id) {
 }
 
 vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts, vr_counters* d_counters) {
+    NvtxRange range_("vr_batch_render");
     if (!ctx) return VR_ERR_INVALID_ARG;
     auto it = ctx->batches.find(batch_id);
     if (it == ctx->batches.end()) return fail(ctx, VR_ERR_INVALID_ARG, "batch_render: unknown batch %d", batch_id);
@@ -971,6 +993,7 @@ vr_status vr_batch_render(vr_ctx* ctx, int batch_id, const vr_render_opts* opts,
 }
 
 vr_status vr_batch_render_graph(vr_ctx* ctx, int batch_id, const vr_render_opts* opts) {
+    NvtxRange range_("vr_batch_render_graph");
     if (!ctx) return VR_ERR_INVALID_ARG;
     auto it = ctx->batches.find(batch_id);
     if (it == ctx->batches.end())
