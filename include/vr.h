@@ -47,7 +47,8 @@ typedef enum {
     VR_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel failed */
     VR_ERR_OOM = 4,         /* device allocation failed */
     VR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    VR_ERR_DEGENERATE = 6   /* I_max == I_min: Eq. 1 is undefined */
+    VR_ERR_DEGENERATE = 6,  /* I_max == I_min: Eq. 1 is undefined */
+    VR_ERR_BOUNDS = 7       /* debug library only: a kernel's index check failed */
 } vr_status;
 
 typedef enum { VR_F32 = 0, VR_U16 = 1 } vr_dtype;
@@ -395,6 +396,22 @@ vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes);
  * VR_ERR_TIMEOUT and clears the word, and the context stays usable.
  * Errors: INVALID_ARG (budget out of range), CUDA. Asynchronous. */
 vr_status vr_probe_bounded_wait(vr_ctx* ctx, long long budget_cycles);
+
+/* 1 in the debug library (libvr_debug.so, built with VR_DEBUG), 0 in libvr.so.
+ * The debug library checks the indices of the raymarch kernels' memory accesses
+ * (brick coordinates, transfer-function cells, voxel and image offsets, the
+ * staged kernel's shared-memory slots, batch view ids); a failed check skips the
+ * access, sets a bit in the context's device status word and records the source
+ * line, and the next vr_synchronize returns VR_ERR_BOUNDS with that line in
+ * vr_last_error. It computes the same images as libvr.so; libvr.so compiles the
+ * checks away. */
+int vr_debug_build(void);
+
+/* Exercise the debug library's index-check reporting: one thread fails one check
+ * (no memory is accessed either way), so the next vr_synchronize returns
+ * VR_ERR_BOUNDS in the debug library and VR_OK in libvr.so. Asynchronous.
+ * Errors: CUDA. */
+vr_status vr_debug_check_probe(vr_ctx* ctx);
 
 /* Device memory held by the context: every buffer the library allocates for it
  * (volumes, derived bricks, cell grids, vesselness, batches, scratch) is counted

@@ -7,6 +7,7 @@ built library these calls raise.
 """
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -69,8 +70,14 @@ def cameras_to_c(cams):
 class Context:
     """One vr_ctx bound to a CUDA device and stream (torch's current stream by default)."""
 
-    def __init__(self, device=0, stream=None):
-        self._lib = _vr.load()
+    def __init__(self, device=0, stream=None, debug=None):
+        """A library context on a CUDA device. debug=True runs the same calls through
+        libvr_debug.so, whose kernels check their memory indices (a failed check is
+        reported by synchronize() as VR_ERR_BOUNDS, and by close()); the default,
+        None, takes the environment variable VR_DEBUG_LIB (1 = debug library)."""
+        if debug is None:
+            debug = os.environ.get("VR_DEBUG_LIB", "0") == "1"
+        self._lib = _vr.load(debug)
         h = ctypes.c_void_p()
         st = self._lib.vr_create(ctypes.byref(h), int(device), _stream_handle(stream))
         if st != 0:
@@ -87,9 +94,19 @@ class Context:
             raise VRError(st, msg.decode() if msg else "")
 
     def close(self):
+        """Destroy the context. With the debug library, first synchronise and raise
+        the failure of any index check still unreported."""
         if getattr(self, "_h", None):
+            st, msg = 0, ""
+            if self._lib.vr_debug_build():
+                st = self._lib.vr_synchronize(self._h)
+                if st != 0:
+                    m = self._lib.vr_last_error(self._h)
+                    msg = m.decode() if m else ""
             self._lib.vr_destroy(self._h)
             self._h = None
+            if st != 0:
+                raise VRError(st, msg)
 
     def __del__(self):
         try:
@@ -267,6 +284,15 @@ class Context:
         """Largest derived-brick store (bytes) later precompute_morphology calls build;
         0 = none (per-sample stencils)."""
         self._check(self._lib.vr_set_derived_budget(self._h, int(nbytes)))
+
+    def debug_check_probe(self):
+        """Fail one kernel index check: synchronize() then raises VR_ERR_BOUNDS in the
+        debug library and nothing in the release one."""
+        self._check(self._lib.vr_debug_check_probe(self._h))
+
+    @property
+    def is_debug(self):
+        return bool(self._lib.vr_debug_build())
 
     def memory_used(self):
         """Device bytes the library holds for this context (see vr_memory_used)."""

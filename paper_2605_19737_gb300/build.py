@@ -2,7 +2,9 @@
 
 Each translation unit under csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo) and linked into
-paper_2605_19737_gb300/libvr.so. Nothing here needs a GPU.
+paper_2605_19737_gb300/libvr.so; the same sources with -DVR_DEBUG (kernel index
+checks that report through the context's status word) give libvr_debug.so.
+Nothing here needs a GPU.
 """
 
 import concurrent.futures as cf
@@ -16,6 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libvr.so")
+OUT_DEBUG = os.path.join(PKG, "libvr_debug.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,18 +46,25 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False):
-    """Build libvr.so if any source or header changed; return its path."""
+def build(force=False, verbose=False, debug=None):
+    """Build libvr.so (debug=False), libvr_debug.so (debug=True) or both (None, the
+    default), recompiling only translation units whose source or headers changed.
+    Returns the path of libvr.so (of libvr_debug.so when debug=True)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
-    objs, jobs = [], []
-    for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + headers):
-            jobs.append([nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj])
+    variants = {False: [False], True: [True], None: [False, True]}[debug]
+    links, jobs = [], []
+    for dbg in variants:
+        bdir = os.path.join(BUILD, "debug") if dbg else BUILD
+        os.makedirs(bdir, exist_ok=True)
+        objs = []
+        for src in sources():
+            obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+            objs.append(obj)
+            if force or _stale(obj, [src] + headers):
+                jobs.append([nvcc] + ARCH + FLAGS + (["-DVR_DEBUG"] if dbg else []) + ["-c", src, "-o", obj])
+        links.append((OUT_DEBUG if dbg else OUT, objs))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -66,11 +76,12 @@ def build(force=False, verbose=False):
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(OUT, objs):
-        tmp = OUT + ".tmp%d" % os.getpid()
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, OUT)
-    return OUT
+    for out, objs in links:
+        if force or jobs or _stale(out, objs):
+            tmp = out + ".tmp%d" % os.getpid()
+            run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
+            os.replace(tmp, out)
+    return OUT_DEBUG if debug else OUT
 
 
 if __name__ == "__main__":

@@ -318,12 +318,15 @@ vr_status vr_synchronize(vr_ctx* ctx) {
     DeviceGuard g(ctx->device);
     CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
     CK(cudaGetLastError(), "asynchronous error");
-    unsigned status = 0;
-    CK(cudaMemcpy(&status, ctx->d_work + 1, sizeof status, cudaMemcpyDeviceToHost), "status word");
-    if (status) {
+    unsigned status[2] = {0, 0};  // status bits, source line of the first failed index check
+    CK(cudaMemcpy(status, ctx->d_work + 1, sizeof status, cudaMemcpyDeviceToHost), "status word");
+    if (status[0] || status[1]) {
         CK(cudaMemset(ctx->d_work + 1, 0, sizeof status), "status word reset");
-        if (status & kStatusTimeout)
+        if (status[0] & kStatusTimeout)
             return fail(ctx, VR_ERR_TIMEOUT, "a bounded device-side wait expired (bulk copy did not complete)");
+        if (status[0] & kStatusBounds)
+            return fail(ctx, VR_ERR_BOUNDS, "debug build: an index check failed at line %u of a kernel source",
+                        status[1]);
     }
     return VR_OK;
 }
@@ -536,6 +539,7 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
     d.gk = (float)((double)tp->gamma / (double)tp->kappa_ref);
     d.inv_kref = (float)(1.0 / (double)tp->kappa_ref);
     d.ka = tp->ka, d.kd = tp->kd, d.ks = tp->ks;
+    d.status = ctx->d_work + 1;
     d.opacity_scale = tp->opacity_scale, d.et_threshold = tp->et_threshold, d.step_vox = tp->step_vox;
     {
         const double smin = fmin((double)v->s[0], fmin((double)v->s[1], (double)v->s[2]));
@@ -1089,6 +1093,21 @@ vr_status vr_fma_peak(vr_ctx* ctx, int blocks, int iters, int reps, float* h_ms,
 vr_status vr_set_derived_budget(vr_ctx* ctx, unsigned long long bytes) {
     if (!ctx) return VR_ERR_INVALID_ARG;
     ctx->derived_budget = (size_t)bytes;
+    return VR_OK;
+}
+
+int vr_debug_build(void) {
+#ifdef VR_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+vr_status vr_debug_check_probe(vr_ctx* ctx) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    CK(launch_check_probe(ctx->d_work + 1, ctx->stream), "index-check probe");
     return VR_OK;
 }
 

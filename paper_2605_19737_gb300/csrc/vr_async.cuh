@@ -11,6 +11,7 @@ namespace vr {
 
 constexpr long long kWaitBudgetCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr unsigned kStatusTimeout = 1u;
+constexpr unsigned kStatusBounds = 2u;  // debug builds: an index check failed
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));

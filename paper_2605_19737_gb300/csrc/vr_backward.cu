@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
             const float2 st = __ldg(L.ray_state + pix);
             kstop = __float_as_int(st.x);
             Tk = st.y;
+            if (!VR_CHECK(L.tp.status, kstop >= -1 && kstop < r.ns)) kstop = -1;  // a state of another image
         } else {
             float A = 0.f, A_prev = 0.f;
             int k = 0, klast = -1;
@@ -208,6 +209,10 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                     sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
                     bc[q] = i0[q] >> 3;
                 }
+                if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
+                                               (unsigned)i0[1] <= (unsigned)(v.n[1] - 2) &&
+                                               (unsigned)i0[2] <= (unsigned)(v.n[2] - 2)))
+                    break;
                 const long long bi = bidx(v, bc);
                 if (L.skip && __ldg(v.empty + bi)) {
                     k = brick_exit_k(r, bc, k, r.ns);
@@ -249,6 +254,10 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 }
                 // No skipping here: a sample in an empty brick has alpha = 0, but its lookup
                 // still gives the opacity entries it reads a non-zero gradient.
+                if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
+                                               (unsigned)i0[1] <= (unsigned)(v.n[1] - 2) &&
+                                               (unsigned)i0[2] <= (unsigned)(v.n[2] - 2)))
+                    continue;
                 const long long bi = bidx(v, bc);
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
@@ -364,6 +373,10 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
                 sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
                 bc[q] = i0[q] >> 3;
             }
+            if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
+                                           (unsigned)i0[1] <= (unsigned)(v.n[1] - 2) &&
+                                           (unsigned)i0[2] <= (unsigned)(v.n[2] - 2)))
+                break;
             const long long bi = bidx(v, bc);
             if (L.skip && __ldg(v.empty + bi)) {
                 k = brick_exit_k(r, bc, k, r.ns);
@@ -416,6 +429,11 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
             while (true) {
                 const int base = ((i0[2] - kCells * sc[2]) * kEdge + (i0[1] - kCells * sc[1])) * kEdge +
                                  (i0[0] - kCells * sc[0]);
+                // the 4^3 stencil and its adjoint touch base + a + 12 b + 144 c, a, b, c in [0, 3]
+                if (!VR_CHECK(L.tp.status, base >= 0 && base + 3 * (1 + kEdge + kEdge * kEdge) < kBrickVox)) {
+                    live = false;
+                    break;
+                }
                 float fld[10];
                 field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
                 scale_field(fld, is);

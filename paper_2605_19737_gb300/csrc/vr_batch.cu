@@ -32,6 +32,7 @@ __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
         const int local = (int)item - __ldg(B.packet_prefix + lo);
         const int npx = (vw.W + B.packet_w - 1) / B.packet_w;
         const int px = local % npx, py = local / npx;
+        if (!VR_CHECK(vw.tp.status, local >= 0 && py * B.packet_h < vw.H)) continue;
         const int i = px * B.packet_w + lane % B.packet_w, j = py * B.packet_h + lane / B.packet_w;
         const bool inside = i < vw.W && j < vw.H;
         const VolumeDev& v = vw.vol;

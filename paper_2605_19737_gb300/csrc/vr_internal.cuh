@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "vr.h"
+#include "vr_async.cuh"
 
 namespace vr {
 
@@ -39,7 +40,25 @@ struct TissueDev {
     float gamma, kappa_ref, w_max, ka, kd, ks, opacity_scale, et_threshold, step_vox;
     float alpha_exp;  // dt / opacity_ref_step for the step-size opacity correction; 0 = off
     float gk, inv_kref;  // gamma / kappa_ref and 1 / kappa_ref (rounded from double on the host)
+    unsigned* status;    // the context's device status word (debug builds report failed index checks there)
 };
+
+// Index checks of the debug library (VR_DEBUG): VR_CHECK(status, cond) is cond,
+// and when cond is false it also sets kStatusBounds in status[0] and records the
+// source line of the first failed check in status[1]; the caller skips the access.
+// Without VR_DEBUG it is the constant true and the check compiles away.
+#ifdef VR_DEBUG
+__device__ __forceinline__ bool debug_check(bool ok, unsigned* status, int line) {
+    if (!ok && status) {
+        atomicOr(status, kStatusBounds);
+        atomicCAS(status + 1, 0u, (unsigned)line);
+    }
+    return ok;
+}
+#define VR_CHECK(status, cond) ::vr::debug_check((cond), (status), __LINE__)
+#else
+#define VR_CHECK(status, cond) true
+#endif
 
 // Per-volume constants that kernels read from device memory (so that host code
 // never waits for the reductions that produce them).
@@ -185,6 +204,8 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t st);
 cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStream_t st);
+// One thread fails one index check (debug builds record it; release builds do nothing).
+cudaError_t launch_check_probe(unsigned* status, cudaStream_t st);
 cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
                                       cudaStream_t st);
 cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,

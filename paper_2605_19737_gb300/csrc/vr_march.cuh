@@ -66,6 +66,11 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
             bc[q] = i0[q] >> 3;
         }
+        if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&
+                                     (unsigned)bc[2] < (unsigned)v.nb[2])) {
+            ++k;
+            continue;
+        }
         const int bi = brick_index(v, bc);
         if (bi != cur_bi) {
             cur_bi = bi;

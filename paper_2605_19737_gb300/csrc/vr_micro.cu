@@ -41,7 +41,17 @@ __global__ void k_wait_probe(unsigned* __restrict__ status, long long budget) {
     }
 }
 
+// Fails one index check; nothing is read or written either way.
+__global__ void k_check_probe(unsigned* status) {
+    if (!VR_CHECK(status, threadIdx.x != 0)) return;
+}
+
 }  // namespace
+
+cudaError_t launch_check_probe(unsigned* status, cudaStream_t st) {
+    k_check_probe<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStream_t st) {
     k_wait_probe<<<1, 32, 0, st>>>(status, budget_cycles);

@@ -161,6 +161,12 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
                     sample_cell(r, q, kk, v.n[q], i0, f);
                     bc[q] = i0 >> 3;
                 }
+                if (!VR_CHECK(L.tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] &&
+                                               (unsigned)bc[1] < (unsigned)v.nb[1] &&
+                                               (unsigned)bc[2] < (unsigned)v.nb[2])) {
+                    live = false;
+                    break;
+                }
                 const int bi = (int)brick_index(v, bc);
                 if (L.skip && __ldg(v.empty + bi)) {
                     k = brick_exit_k(r, bc, k, r.ns);
@@ -213,6 +219,11 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
                     }
                     const int base = ((i0[2] - kCells * sc[2]) * kEdge + (i0[1] - kCells * sc[1])) * kEdge +
                                      (i0[0] - kCells * sc[0]);
+                    // the 4^3 stencil reads base + a + 12 b + 144 c, a, b, c in [0, 3]
+                    if (!VR_CHECK(L.tp.status, base >= 0 && base + 3 * (1 + kEdge + kEdge * kEdge) < kBrickVox)) {
+                        live = false;
+                        break;
+                    }
                     float fld[10];
                     field_eval(SmemLoad{sbrick}, base, f[0], f[1], f[2], fld);
                     scale_field(fld, is);

@@ -297,6 +297,7 @@ __device__ __forceinline__ void optics_tf(const float f[4], float vval, const Ti
     const int w = tp.tf_w, h = tp.tf_h;
     const float xs = fminf(fmaxf(f[0], 0.0f), 1.0f) * (float)(w - 1);
     o.j = min((int)xs, w - 2);
+    if (!VR_CHECK(tp.status, o.j >= 0)) o.j = 0;
     o.t = xs - (float)o.j;
     if (h == 1) {
         o.k = 0;
@@ -308,6 +309,7 @@ __device__ __forceinline__ void optics_tf(const float f[4], float vval, const Ti
     } else {
         const float ys = fminf(fmaxf(o.y, 0.0f), 1.0f) * (float)(h - 1);
         o.k = min((int)ys, h - 2);
+        if (!VR_CHECK(tp.status, o.k >= 0)) o.k = 0;
         o.q = ys - (float)o.k;
         const float4* r0 = tf + (long long)o.k * w + o.j;
         o.T00 = __ldg(r0);

@@ -11,14 +11,16 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvr.so")
+LIB_DEBUG_PATH = os.path.join(_HERE, "libvr_debug.so")
 
-VR_OK, VR_ERR_INVALID_ARG, VR_ERR_NOT_READY, VR_ERR_CUDA, VR_ERR_OOM, VR_ERR_TIMEOUT, VR_ERR_DEGENERATE = range(7)
+VR_OK, VR_ERR_INVALID_ARG, VR_ERR_NOT_READY, VR_ERR_CUDA, VR_ERR_OOM, VR_ERR_TIMEOUT, VR_ERR_DEGENERATE, VR_ERR_BOUNDS = \
+    range(8)
 VR_F32, VR_U16 = 0, 1
 VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL = 0, 1, 2
 VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_NOT_READY", 3: "VR_ERR_CUDA", 4: "VR_ERR_OOM",
-                5: "VR_ERR_TIMEOUT", 6: "VR_ERR_DEGENERATE"}
+                5: "VR_ERR_TIMEOUT", 6: "VR_ERR_DEGENERATE", 7: "VR_ERR_BOUNDS"}
 
 
 class vr_camera(ctypes.Structure):
@@ -83,6 +85,8 @@ SIGNATURES = {
     "vr_classify_bricks_noalloc": ([_P, _LL, _P, _I, _I, _P, _P, ctypes.c_char_p, _I], _I),
     "vr_set_derived_budget": ([_P, ctypes.c_ulonglong], _I),
     "vr_probe_bounded_wait": ([_P, _LL], _I),
+    "vr_debug_build": ([], _I),
+    "vr_debug_check_probe": ([_P], _I),
     "vr_memory_used": ([_P, ctypes.POINTER(ctypes.c_ulonglong)], _I),
     "vr_set_memory_limit": ([_P, ctypes.c_ulonglong], _I),
     "vr_debug_fail_alloc": ([_P, _LL, ctypes.POINTER(_LL)], _I),
@@ -95,22 +99,23 @@ SIGNATURES = {
     "vr_render_backward": ([_P, _I, _P, _I, _I, _I, _P, _P, _P, _P, ctypes.POINTER(vr_render_opts)], _I),
 }
 
-_lib = None
+_libs = {}
 
 
-def load():
-    """Load libvr.so (raises if it is missing: the CUDA library is required)."""
-    global _lib
-    if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError("libvr.so not built at %s; run paper_2605_19737_gb300.build.build()" % LIB_PATH)
-        lib = ctypes.CDLL(LIB_PATH)
+def load(debug=False):
+    """Load libvr.so, or with debug=True libvr_debug.so (the same library with kernel
+    index checks); raises if it is missing: the CUDA library is required."""
+    path = LIB_DEBUG_PATH if debug else LIB_PATH
+    if path not in _libs:
+        if not os.path.exists(path):
+            raise ImportError("%s not built; run paper_2605_19737_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
         for name, (args, res) in SIGNATURES.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = res
-        _lib = lib
-    return _lib
+        _libs[path] = lib
+    return _libs[path]
 
 
 def exported_symbols():

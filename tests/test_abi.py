@@ -33,9 +33,17 @@ def test_header_declares_core_calls():
 
 
 def test_library_exports_every_declared_symbol(libpath):
-    lib = ctypes.CDLL(libpath)
-    missing = [n for n in _declared() if not hasattr(lib, n)]
-    assert not missing, missing
+    from paper_2605_19737_gb300 import build
+    for path in (libpath, build.OUT_DEBUG):
+        lib = ctypes.CDLL(path)
+        missing = [n for n in _declared() if not hasattr(lib, n)]
+        assert not missing, (path, missing)
+
+
+def test_debug_library_is_the_checked_build(libpath):
+    from paper_2605_19737_gb300 import vr
+    assert vr.load().vr_debug_build() == 0
+    assert vr.load(debug=True).vr_debug_build() == 1
 
 
 def test_binding_matches_header(libpath):
