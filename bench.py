@@ -137,23 +137,30 @@ def _json_line(d):
     print(json.dumps(d), flush=True)
 
 
-def cpu_baseline(case, stride, threads=None):
-    """Time the FP64 oracle on every `stride`-th row/column of the frame."""
+def cpu_baseline(case, stride, threads=None, min_seconds=0.0):
+    """Time the FP64 oracle on every `stride`-th row/column of the frame, repeating
+    the render until at least `min_seconds` have passed (one render at least)."""
     import oracle
     from tests.gpu_util import oracle_params
     if threads:
         os.environ["OMP_NUM_THREADS"] = str(threads)
     In = oracle.normalize(case["volume"])
     t0 = time.perf_counter()
-    res = oracle.render(In, case["spacing"], oracle_params(case["params"], case["tf"]), case["tf"], case["cams"],
-                        case["W"], case["H"], pix_stride=stride, alternatives=False)
-    dt = time.perf_counter() - t0
-    dense = int(res.dense.sum())
+    dense, reps = 0, 0
+    while True:
+        res = oracle.render(In, case["spacing"], oracle_params(case["params"], case["tf"]), case["tf"], case["cams"],
+                            case["W"], case["H"], pix_stride=stride, alternatives=False)
+        dense += int(res.dense.sum())
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds:
+            break
     rays = len(range(0, case["H"], stride)) * len(range(0, case["W"], stride))
+    part = ("every %d-th row and column of the %dx%d frame" % (stride, case["W"], case["H"]) if stride > 1
+            else "the whole %dx%d frame" % (case["W"], case["H"]))
     return {"value": dense / dt / 1e9, "unit": UNIT, "cores": int(res.threads), "kind": "oracle",
-            "sample": "every %dth row and column of the %dx%d frame (%d rays, %d dense samples), "
-                      "including the oracle's voxel-derivative setup, %.1f s" % (stride, case["W"], case["H"], rays,
-                                                                               dense, dt),
+            "sample": "%s (%d rays, %d dense samples per render) x %d renders, including the oracle's "
+                      "voxel-derivative setup, %.1f s" % (part, rays, dense // reps, reps, dt),
             "seconds": dt, "dense_samples": dense}
 
 
@@ -171,7 +178,10 @@ def run_reference(args):
     if rank != 0:
         return
     case = workloads.brainweb_1080p()
-    stride = 6
+    # each step renders every stride-th row and column of the frame (about 0.6 s on
+    # 16 cores at stride 2), so that warm-up + timed steps end within a few minutes
+    n = args.warmup + args.steps
+    stride = 2 if n <= 300 else (4 if n <= 1200 else 8)
     vals, last = [], None
     for i in range(args.warmup + args.steps):
         last = cpu_baseline(case, stride)
@@ -477,7 +487,7 @@ def run(args):
     if rank == 0:
         cb = None
         if ws == 1 and not args.no_cpu_baseline:
-            cb = cpu_baseline(workloads.brainweb_1080p(), stride=2)
+            cb = cpu_baseline(workloads.brainweb_1080p(), stride=1, min_seconds=10.0)
             cb.pop("seconds", None)
             # and the whole small head frame (64^3, 128x128, 1D TF), every pixel
             small = cpu_baseline(workloads.head64_128px(), stride=1)
