@@ -70,7 +70,7 @@ struct vr_ctx {
     int partials_cap = 0;
     void* d_stage = nullptr;
     size_t stage_cap = 0;
-    float* d_scratch = nullptr;   // vesselness scratch (smoothed volume + 3 eigenvalue planes), prefilter
+    float* d_scratch = nullptr;   // vesselness scratch (smoothed volume + smoothing pass), prefilter
     size_t scratch_cap = 0;
     float* d_tfgrad = nullptr;    // private copies of a 2D transfer-function gradient
     size_t tfgrad_cap = 0;
@@ -470,7 +470,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
         if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
         if (!v->d_smax) CK(dalloc(ctx, &v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
-        const size_t need = sizeof(float) * 4 * (size_t)v->nvox;  // smoothed volume + 3 eigenvalue planes
+        const size_t need = sizeof(float) * 2 * (size_t)v->nvox;  // smoothed volume + smoothing pass
         if (ctx->scratch_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "vesselness scratch sync");
             dfree(ctx, ctx->d_scratch);

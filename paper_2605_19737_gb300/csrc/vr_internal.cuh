@@ -184,8 +184,8 @@ cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3
 cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, const int* prefix, int tf_w,
                                   uint32_t* cellmask, cudaStream_t st);
 
-// Multi-scale vesselness of `norm` into V (both nvox floats); tmp_a is nvox and
-// tmp_b 3 nvox floats of scratch, smax receives each scale's max Hessian norm.
+// Multi-scale vesselness of `norm` into V (both nvox floats); tmp_a and tmp_b are
+// nvox floats of scratch each, smax receives each scale's max Hessian norm.
 cudaError_t launch_frangi(const float* norm, const int n[3], const float* sigmas, int n_sigmas, float* tmp_a,
                           float* tmp_b, float* smax, float* V, cudaStream_t st);
 

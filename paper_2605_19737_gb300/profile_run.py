@@ -25,17 +25,21 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="brainweb_1080p",
-                    choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam"])
+                    choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam", "vessel_1080p"])
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=4)
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--backward", action="store_true", help="also run the adjoint raymarch after each frame")
+    ap.add_argument("--precompute-reps", type=int, default=1,
+                    help="run the morphology precompute this many times (timed with CUDA events)")
     args = ap.parse_args()
     if args.workload == "head64":
         case = workloads.head64_128px()
     elif args.workload == "diff_head128_8cam":
         case = workloads.diff_head128_8cam()
+    elif args.workload == "vessel_1080p":
+        case = workloads.vessel_1080p()
     elif args.workload == "brainweb_540p":
         case = workloads.brainweb_1080p(width=960, height=540)
     else:
@@ -46,7 +50,15 @@ def main():
     data = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
     with pkg.Context(0) as ctx:
         vid = ctx.load_volume(data, case["spacing"])
-        ctx.precompute_morphology(vid, case["sigmas"])
+        tp = []
+        for _ in range(args.precompute_reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            ctx.precompute_morphology(vid, case["sigmas"])
+            e.record()
+            ctx.synchronize()
+            tp.append(s.elapsed_time(e))
+        print("%s precompute (sigmas %s): %.3f ms (last of %d)" % (args.workload, case["sigmas"], tp[-1], len(tp)))
         ctx.set_tissue_params(vid, case["tf"], **case["params"])
         out = torch.empty((case["cams"].shape[0], case["H"], case["W"], 4), device="cuda")
         dl = torch.randn(out.shape, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
