@@ -199,6 +199,18 @@ vr_status vr_free_volume(vr_ctx* ctx, int vol_id);
  * Errors: INVALID_ARG, OOM, CUDA. */
 vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigmas, int n_sigmas);
 
+/* Second channel of a loaded volume: a co-registered scalar volume of the same
+ * dims (a second MRI contrast or another modality, Sec. 5.4's multi-parametric
+ * extension), normalised by its own I_min, I_max (Eq. 1) and bricked like the
+ * first. It takes the place of the vesselness channel: VR_TF_2D_VESSEL then
+ * renders over (I_norm, second channel), and whichever of this call and a
+ * vr_precompute_morphology with n_sigmas > 0 ran last defines that channel.
+ * data: nx*ny*nz values of `dtype`, x fastest, host or device (on_device);
+ * copied. Reads I_min/I_max back (synchronises). Tissue params in mode 2 must be
+ * set again afterwards. Errors: INVALID_ARG, DEGENERATE (a constant channel),
+ * OOM, CUDA; after an error mode 2 is NOT_READY until a channel is loaded. */
+vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int on_device, vr_dtype dtype);
+
 /* Set transfer-function and tissue uniforms (copied), then re-classify the
  * bricks (and, with derived bricks, the cells) for empty-space skipping: two
  * small kernels, tens of microseconds. Nothing else is recomputed (the uniform
@@ -226,7 +238,8 @@ vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm);
  *   h_nb: 3 ints (nbx, nby, nbz). Any of them may be NULL. */
 vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb);
 
-/* Copy the vesselness volume (nx*ny*nz float32) to `out` (device if
+/* Copy the second channel -- the vesselness volume, or the normalised channel of
+ * vr_load_second_channel -- (nx*ny*nz float32) to `out` (device if
  * out_on_device, else host; synchronises for host). NOT_READY without it. */
 vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_device);
 

@@ -222,6 +222,24 @@ class Context:
         self._check(self._lib.vr_get_vesselness(self._h, vol, out.data_ptr(), 1))
         return out
 
+    def load_second_channel(self, vol, data):
+        """A co-registered second channel (same (nz, ny, nx) shape; float32 or uint16,
+        host or device), normalised by its own min/max; tf_mode 2 then renders over
+        (I_norm, channel). Replaces the vesselness channel (and vice versa)."""
+        nx, ny, nz = self._keep[vol]
+        if tuple(data.shape) != (nz, ny, nx):
+            raise ValueError("second channel must have shape %s" % ((nz, ny, nx),))
+        if isinstance(data, np.ndarray):
+            dt = VR_F32 if data.dtype == np.float32 else (VR_U16 if data.dtype == np.uint16 else None)
+        else:
+            torch = _torch()
+            dt = VR_F32 if data.dtype == torch.float32 else (
+                VR_U16 if data.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)) else None)
+        if dt is None:
+            raise TypeError("channel must be float32 or uint16")
+        p, dev = _ptr(data)
+        self._check(self._lib.vr_load_second_channel(self._h, vol, p, int(dev), dt))
+
     def prefilter(self, vol, mode="median", sigma=1.0):
         """Replace I_norm by its 3x3x3 median ("median") or Gaussian ("gauss", sigma voxels)."""
         m = {"median": 1, "gauss": 2}[mode]

@@ -40,6 +40,8 @@ struct Volume {
     uint16_t* d_cellq = nullptr;     // after the morphology precompute: per-cell quantised min/max
     uint32_t* d_cellmask = nullptr;  // and per-cell empty bits under the current transfer function
     float* d_smax = nullptr;  // per-scale max Hessian norm (8 floats)
+    float* d_ch2 = nullptr;   // second channel: [0, 2) its I_min, I_max, [4, 8) its VolConst
+    bool v_ready = false;     // d_vessel holds a complete second channel (vesselness or a modality)
     float* d_tf = nullptr;
     size_t tf_cap = 0;
     int* d_prefix = nullptr;
@@ -163,6 +165,7 @@ void free_volume(vr_ctx* ctx, Volume* v) {
     dfree(ctx, v->d_cellq);
     dfree(ctx, v->d_cellmask);
     dfree(ctx, v->d_smax);
+    dfree(ctx, v->d_ch2);
     dfree(ctx, v->d_tf);
     dfree(ctx, v->d_prefix);
     delete v;
@@ -467,6 +470,8 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         if (cs != VR_OK) return cs;
     }
     if (n_sigmas > 0) {
+        v->v_ready = false;
+        if (v->params_ready && v->tp.tf_mode == 2) v->params_ready = false;  // its V channel is being replaced
         if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
         if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
         if (!v->d_smax) CK(dalloc(ctx, &v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
@@ -483,6 +488,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
                          v->d_vessel, ctx->stream),
            "vesselness");
         CK(launch_make_bricks(v->d_vessel, v->n, v->nb, v->d_vbricks, ctx->stream), "vesselness bricks");
+        v->v_ready = true;
     }
     v->morph_ready = true;
     return VR_OK;
@@ -498,8 +504,9 @@ vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* 
     if (tp->tf_w < 2 || tp->tf_w > 4096) return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: tf_w outside [2, 4096]");
     if (tp->tf_mode == 0 ? tp->tf_h != 1 : (tp->tf_h < 2 || tp->tf_h > 256))
         return fail(ctx, VR_ERR_INVALID_ARG, "set_tissue_params: tf_h %d invalid for mode %d", tp->tf_h, tp->tf_mode);
-    if (tp->tf_mode == 2 && !v->d_vessel)
-        return fail(ctx, VR_ERR_NOT_READY, "set_tissue_params: vesselness mode needs precomputed vesselness");
+    if (tp->tf_mode == 2 && !v->v_ready)
+        return fail(ctx, VR_ERR_NOT_READY,
+                    "set_tissue_params: mode 2 needs precomputed vesselness or a second channel");
     if (!finite_pos(tp->kappa_ref) || !(tp->w_max >= 0.0f) || !isfinite(tp->gamma) || !finite_pos(tp->step_vox) ||
         !(tp->opacity_scale >= 0.0f) || !isfinite(tp->opacity_scale) || !isfinite(tp->et_threshold) ||
         !isfinite(tp->ka) || !isfinite(tp->kd) || !isfinite(tp->ks))
@@ -594,6 +601,46 @@ vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm) {
     return VR_OK;
 }
 
+vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int on_device, vr_dtype dtype) {
+    NvtxRange range_("vr_load_second_channel");
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "load_second_channel: unknown id %d", vol_id);
+    if (!data) return fail(ctx, VR_ERR_INVALID_ARG, "load_second_channel: NULL pointer");
+    if (dtype != VR_F32 && dtype != VR_U16) return fail(ctx, VR_ERR_INVALID_ARG, "load_second_channel: bad dtype");
+    DeviceGuard g(ctx->device);
+    // until the channel is complete, neither it nor tissue params that render over it are usable
+    v->v_ready = false;
+    if (v->params_ready && v->tp.tf_mode == 2) v->params_ready = false;
+    if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "load_second_channel: channel volume");
+    if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "load_second_channel: bricks");
+    if (!v->d_ch2) CK(dalloc(ctx, &v->d_ch2, sizeof(float) * 8), "load_second_channel: normalisation constants");
+    const size_t esz = dtype == VR_F32 ? 4 : 2;
+    const void* raw = data;
+    if (!on_device) {
+        CK(ensure_stage(ctx, esz * v->nvox), "load_second_channel: staging buffer");
+        CK(cudaMemcpyAsync(ctx->d_stage, data, esz * v->nvox, cudaMemcpyHostToDevice, ctx->stream),
+           "load_second_channel: copy");
+        raw = ctx->d_stage;
+    }
+    // Eq. 1 applied to the channel itself: its own I_min, I_max
+    vr_status st = vr_reduce_minmax(ctx, raw, dtype, v->nvox, v->d_ch2);
+    if (st != VR_OK) return st;
+    CK(launch_normalize(raw, dtype, v->nvox, v->d_ch2, reinterpret_cast<VolConst*>(v->d_ch2 + 4), v->d_vessel,
+                        ctx->stream),
+       "load_second_channel: normalise");
+    CK(launch_make_bricks(v->d_vessel, v->n, v->nb, v->d_vbricks, ctx->stream), "load_second_channel: bricking");
+    float mm[2] = {0, 0};
+    CK(cudaMemcpyAsync(mm, v->d_ch2, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream), "load_second_channel: read back");
+    CK(cudaStreamSynchronize(ctx->stream), "load_second_channel: sync");
+    if (!(isfinite(mm[0]) && isfinite(mm[1])))
+        return fail(ctx, VR_ERR_INVALID_ARG, "load_second_channel: non-finite intensities");
+    if (!(mm[1] > mm[0]))
+        return fail(ctx, VR_ERR_DEGENERATE, "load_second_channel: I_max == I_min (%g); Eq. 1 undefined", (double)mm[0]);
+    v->v_ready = true;
+    return VR_OK;
+}
+
 vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb) {
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
@@ -613,7 +660,7 @@ vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_devi
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v || !out) return fail(ctx, VR_ERR_INVALID_ARG, "get_vesselness: bad arguments");
-    if (!v->d_vessel) return fail(ctx, VR_ERR_NOT_READY, "get_vesselness: no vesselness computed");
+    if (!v->v_ready) return fail(ctx, VR_ERR_NOT_READY, "get_vesselness: no vesselness or second channel");
     DeviceGuard g(ctx->device);
     CK(cudaMemcpyAsync(out, v->d_vessel, sizeof(float) * v->nvox,
                        out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
