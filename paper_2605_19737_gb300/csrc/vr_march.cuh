@@ -102,10 +102,13 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
         float fld[10], alpha, col[3];
         if (kDerived) {
-            // I and the gradient first (one 16-byte load per corner), then the transfer
-            // function: a zero opacity entry makes alpha exactly 0 whatever the Hessian,
-            // and the sample adds nothing (bit-neutral), so its Hessian is never read
+            // I and the gradient (one 16-byte load per corner) and the Hessian (two), then
+            // the transfer function: a zero opacity entry makes alpha exactly 0 whatever
+            // the Hessian, and the sample adds nothing (bit-neutral). The Hessian loads are
+            // issued before that test so that they overlap the table lookup (measured:
+            // equal at 1080p, 2 % faster on the 8-view workload than loading them after it)
             derived_channels<kParity, 0, 4>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld);
+            load_hessian<kParity>(tp, dbrick, lx, ly, lz, f, fld);
             SampleOptics o;
             optics_tf(fld, vval, tp, tf, inv_gmax, o);
             if (o.c.w == 0.0f) {
@@ -113,7 +116,6 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
                 ++k;
                 continue;
             }
-            load_hessian<kParity>(tp, dbrick, lx, ly, lz, f, fld);
             optics_rest(fld, r.dir, tp, o);
             alpha = o.alpha;
             col[0] = o.col[0];

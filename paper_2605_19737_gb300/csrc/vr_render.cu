@@ -16,10 +16,12 @@ namespace vr {
 
 namespace {
 
-// 7 resident CTAs per SM for the derived-brick path (<= 72 registers; at 1080p 2.46 ms
-// against 2.53 ms for 8 CTAs at 64 registers), 6 for the stencils.
+// Resident CTAs per SM: 8 for the derived-brick path (<= 64 registers: equal at 1080p,
+// 2.5 % faster on the 8-view 512^2 workload than 7 at 72 registers), 7 when it also
+// records the ray state (64 registers would spill 64 bytes), 6 for the stencils.
 template <bool kDerived, bool kState>
-__global__ void __launch_bounds__(128, kDerived ? 7 : 6) k_render_gather(const __grid_constant__ RenderLaunch L) {
+__global__ void __launch_bounds__(128, kDerived ? (kState ? 7 : 8) : 6)
+    k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
     tile_pixel(L.packet_w, w, l, di, dj);
