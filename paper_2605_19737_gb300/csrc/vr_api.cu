@@ -864,7 +864,11 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     B.dvol = d_dvolume;
     {
         // private copies of the transfer-function gradient, summed after the kernels
-        const size_t need = sizeof(float) * ntf * kTfGradCopies;
+        // as many copies as fit 64 MB, 64 to 1024: the fewer the table's entries, the
+        // more CTAs contend for each, and the cheaper a copy is
+        const size_t tbytes = sizeof(float) * ntf;
+        const int ncopies = (int)std::min<size_t>(1024, std::max<size_t>(64, ((size_t)64 << 20) / tbytes));
+        const size_t need = tbytes * ncopies;
         if (ctx->tfgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
             dfree(ctx, ctx->d_tfgrad);
@@ -875,7 +879,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         }
         CK(cudaMemsetAsync(ctx->d_tfgrad, 0, need, ctx->stream), "render_backward: zero scratch");
         B.dtf_copies = ctx->d_tfgrad;
-        B.n_copies = kTfGradCopies;
+        B.n_copies = ncopies;
     }
     for (int c0 = 0; c0 < n_cams; c0 += kMaxCamsPerLaunch) {
         const int nc = n_cams - c0 < kMaxCamsPerLaunch ? n_cams - c0 : kMaxCamsPerLaunch;
@@ -890,7 +894,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (channels)
         CK(launch_channels_to_voxels(ctx->d_dgrad, v->n, v->s, d_dvolume, ctx->stream),
            "render_backward: channel gradients to voxels");
-    CK(launch_sum_copies(ctx->d_tfgrad, kTfGradCopies, (long long)ntf, d_dtf, ctx->stream),
+    CK(launch_sum_copies(ctx->d_tfgrad, B.n_copies, (long long)ntf, d_dtf, ctx->stream),
        "render_backward: sum gradient copies");
     return VR_OK;
 }

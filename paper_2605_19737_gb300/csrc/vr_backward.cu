@@ -519,13 +519,20 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     }
 }
 
-// dtf[e] = sum of the n_copies private copies of entry e.
+// dtf[e] += the sum of copies [16 g, 16 g + 16) of entry e, one thread per (e, g):
+// enough threads for a small table with many copies (dtf is zeroed before).
+constexpr int kCopiesPerThread = 16;
 __global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ copies, int n_copies, long long n,
                                                    float* __restrict__ out) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long groups = (n_copies + kCopiesPerThread - 1) / kCopiesPerThread;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n * groups;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long e = t % n;
+        const int c0 = (int)(t / n) * kCopiesPerThread;
+        const int c1 = min(c0 + kCopiesPerThread, n_copies);
         float acc = 0.0f;
-        for (int c = 0; c < n_copies; ++c) acc += __ldg(copies + (size_t)c * n + e);
-        out[e] = acc;
+        for (int c = c0; c < c1; ++c) acc += __ldg(copies + (size_t)c * n + e);
+        if (acc != 0.0f) atomicAdd(out + e, acc);
     }
 }
 
@@ -541,7 +548,7 @@ cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const 
 }
 
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st) {
-    const long long blocks = (n + 255) / 256;
+    const long long blocks = (n * ((n_copies + kCopiesPerThread - 1) / kCopiesPerThread) + 255) / 256;
     k_sum_copies<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(copies, n_copies, n, dtf);
     return cudaGetLastError();
 }

@@ -136,8 +136,6 @@ struct BackwardLaunch {
     float* dgrad;           // derived-brick path with dvol: zeroed nvox x kDerFloats channel gradients, else nullptr
 };
 
-constexpr int kTfGradCopies = 64;
-
 // One view of a batched render (device-resident table).
 struct ViewDev {
     VolumeDev vol;
