@@ -156,7 +156,8 @@ def cpu_baseline(case, stride, threads=None, min_seconds=0.0):
         if dt >= min_seconds:
             break
     rays = len(range(0, case["H"], stride)) * len(range(0, case["W"], stride))
-    part = ("every %d-th row and column of the %dx%d frame" % (stride, case["W"], case["H"]) if stride > 1
+    nth = {2: "2nd", 3: "3rd"}.get(stride, "%dth" % stride)
+    part = ("every %s row and column of the %dx%d frame" % (nth, case["W"], case["H"]) if stride > 1
             else "the whole %dx%d frame" % (case["W"], case["H"]))
     return {"value": dense / dt / 1e9, "unit": UNIT, "cores": int(res.threads), "kind": "oracle",
             "sample": "%s (%d rays, %d dense samples per render) x %d renders, including the oracle's "
