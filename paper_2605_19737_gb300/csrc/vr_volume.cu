@@ -160,28 +160,37 @@ __global__ void __launch_bounds__(256) k_make_bricks(const float* __restrict__ n
 // the paper's compute shader produces, laid out for 16-byte loads.
 __global__ void __launch_bounds__(256) k_make_derived(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
                                                       int nby, float hx, float hy, float hz, float* __restrict__ out) {
+    // the brick's corner voxels and their neighbours, [8b - 1, 8b + 10) per axis,
+    // clamped to the volume (so neighbour i +- 1 of a corner is tile entry t +- 1)
+    constexpr int kT = kDerEdge + 2;
+    __shared__ float tile[kT * kT * kT];
     const long long b = blockIdx.x;
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
-    const long long row = (long long)ny * nx;
+    const int x0 = kCells * bx - 1, y0 = kCells * by - 1, z0 = kCells * bz - 1;
+    for (int e = threadIdx.x; e < kT * kT * kT; e += blockDim.x) {
+        const int tx = e % kT, ty = (e / kT) % kT, tz = e / (kT * kT);
+        const int x = min(max(x0 + tx, 0), nx - 1), y = min(max(y0 + ty, 0), ny - 1), z = min(max(z0 + tz, 0), nz - 1);
+        tile[e] = __ldg(norm + ((long long)z * ny + y) * nx + x);
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < kDerEdge * kDerEdge * kDerEdge; e += blockDim.x) {
         const int lx = e % kDerEdge, ly = (e / kDerEdge) % kDerEdge, lz = e / (kDerEdge * kDerEdge);
-        const int x = min(kCells * bx + lx, nx - 1), y = min(kCells * by + ly, ny - 1), z = min(kCells * bz + lz, nz - 1);
-        const int xm = max(x - 1, 0), xp = min(x + 1, nx - 1);
-        const int ym = max(y - 1, 0), yp = min(y + 1, ny - 1);
-        const int zm = max(z - 1, 0), zp = min(z + 1, nz - 1);
-        auto at = [&](int i, int j, int k) { return __ldg(norm + (long long)k * row + (long long)j * nx + i); };
-        const float c = at(x, y, z), c2 = 2.0f * c;
+        // the corner voxel (clamped as in the per-voxel definition) in tile coordinates
+        const int tx = min(kCells * bx + lx, nx - 1) - x0, ty = min(kCells * by + ly, ny - 1) - y0,
+                  tz = min(kCells * bz + lz, nz - 1) - z0;
+        auto at = [&](int dx, int dy, int dz) { return tile[((tz + dz) * kT + (ty + dy)) * kT + (tx + dx)]; };
+        const float c = at(0, 0, 0), c2 = 2.0f * c;
         float4 a, m, t;
         a.x = c;
-        a.y = (at(xp, y, z) - at(xm, y, z)) * (0.5f * hx);
-        a.z = (at(x, yp, z) - at(x, ym, z)) * (0.5f * hy);
-        a.w = (at(x, y, zp) - at(x, y, zm)) * (0.5f * hz);
-        m.x = (at(xp, y, z) - c2 + at(xm, y, z)) * (hx * hx);
-        m.y = (at(x, yp, z) - c2 + at(x, ym, z)) * (hy * hy);
-        m.z = (at(x, y, zp) - c2 + at(x, y, zm)) * (hz * hz);
-        m.w = ((at(xp, yp, z) - at(xp, ym, z)) - (at(xm, yp, z) - at(xm, ym, z))) * (0.25f * hx * hy);
-        t.x = ((at(xp, y, zp) - at(xp, y, zm)) - (at(xm, y, zp) - at(xm, y, zm))) * (0.25f * hx * hz);
-        t.y = ((at(x, yp, zp) - at(x, yp, zm)) - (at(x, ym, zp) - at(x, ym, zm))) * (0.25f * hy * hz);
+        a.y = (at(1, 0, 0) - at(-1, 0, 0)) * (0.5f * hx);
+        a.z = (at(0, 1, 0) - at(0, -1, 0)) * (0.5f * hy);
+        a.w = (at(0, 0, 1) - at(0, 0, -1)) * (0.5f * hz);
+        m.x = (at(1, 0, 0) - c2 + at(-1, 0, 0)) * (hx * hx);
+        m.y = (at(0, 1, 0) - c2 + at(0, -1, 0)) * (hy * hy);
+        m.z = (at(0, 0, 1) - c2 + at(0, 0, -1)) * (hz * hz);
+        m.w = ((at(1, 1, 0) - at(1, -1, 0)) - (at(-1, 1, 0) - at(-1, -1, 0))) * (0.25f * hx * hy);
+        t.x = ((at(1, 0, 1) - at(1, 0, -1)) - (at(-1, 0, 1) - at(-1, 0, -1))) * (0.25f * hx * hz);
+        t.y = ((at(0, 1, 1) - at(0, 1, -1)) - (at(0, -1, 1) - at(0, -1, -1))) * (0.25f * hy * hz);
         t.z = 0.0f;
         t.w = 0.0f;
         float4* o = reinterpret_cast<float4*>(out + b * kDerBrickFloats) + 3 * e;
