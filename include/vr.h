@@ -66,7 +66,8 @@ typedef struct {
 typedef enum {
     VR_TF_1D = 0,        /* opacity/colour over I_norm (tf_h == 1) */
     VR_TF_2D_GRAD = 1,   /* over (I_norm, |grad I| / |grad I|_max) */
-    VR_TF_2D_VESSEL = 2  /* over (I_norm, vesselness V); needs vesselness */
+    VR_TF_2D_VESSEL = 2  /* over (I_norm, V): the vesselness, or a second channel
+                            (vr_load_second_channel); needs one of them */
 } vr_tf_mode;
 
 /* Tissue and transfer-function uniforms (Sec. 2.4, Eq. 4; Table 2 windows are
@@ -215,7 +216,9 @@ vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int 
  * bricks (and, with derived bricks, the cells) for empty-space skipping: two
  * small kernels, tens of microseconds. Nothing else is recomputed (the uniform
  * buffers of the abstract and Sec. 4). Errors: INVALID_ARG (bad sizes or
- * values, 2D-vessel mode without vesselness), NOT_READY, OOM, CUDA. */
+ * values), NOT_READY (mode 2 without vesselness or a second channel), OOM, CUDA.
+ * Argument errors change nothing; after an OOM or CUDA error the volume is
+ * NOT_READY for rendering until a call succeeds. */
 vr_status vr_set_tissue_params(vr_ctx* ctx, int vol_id, const vr_tissue_params* tp);
 
 /* I_min, I_max (Eq. 1) and |grad I|_max (Eq. 4) of a volume; any pointer may be
