@@ -271,6 +271,23 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
                 const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
                                        g4.w * P);
+                if (so.c.w == 0.0f) {
+                    // zero opacity entry: alpha = 0 exactly, so only the table's opacity
+                    // entries at the lookup receive a gradient (the one-sided derivative of
+                    // the clamp at 0); colour, uniforms and field gradients are all zero
+                    float dal = da;
+                    if (L.tp.alpha_exp > 0.0f) dal *= L.tp.alpha_exp;
+                    const float dr[4] = {0.f, 0.f, 0.f,
+                                         (so.raw >= 0.0f && so.raw <= 1.0f) ? dal * L.tp.opacity_scale * so.mg * so.wk
+                                                                            : 0.0f};
+                    if (L.tp.tf_h == 1)
+                        sink.add_cell(so.j, 1.0f - so.t, so.t, 0.0f, 0.0f, dr);
+                    else
+                        sink.add_cell(so.k * L.tp.tf_w + so.j, (1.0f - so.q) * (1.0f - so.t), (1.0f - so.q) * so.t,
+                                      so.q * (1.0f - so.t), so.q * so.t, dr);
+                    Tk1 = Tk;
+                    continue;
+                }
                 const float ta = Tk * alpha;
                 const float dc[3] = {ta * dC[0], ta * dC[1], ta * dC[2]};
                 float dfs[10];
