@@ -1,5 +1,5 @@
-// vr_frangi.cu -- per-volume multi-scale Hessian vesselness (the "multi-scale
-// Hessian analysis and vesselness measures" of Sec. 1, read as the
+// vr_frangi.cu -- per-volume multi-scale Hessian vesselness (the multi-scale
+// Hessian analysis with vesselness measures that Sec. 1 mentions, read as the
 // bright-vessel response of Frangi et al., MICCAI 1998), computed once per
 // volume like the paper's morphology compute shader (Sec. 2.3).
 //
