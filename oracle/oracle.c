@@ -1070,6 +1070,9 @@ void or_render_grad(const double *In, const double *V, const int *n, const doubl
             for (int i = 0; i < W; ++i) {
                 int64_t pix = ((int64_t)ci * H + j) * W + i;
                 const double *dl = dl_drgba + 4 * pix;
+                /* every term of a ray's gradient carries a factor of its dl: a ray with
+                 * dl = 0 adds exactly zero and is not marched */
+                if (dl[0] == 0.0 && dl[1] == 0.0 && dl[2] == 0.0 && dl[3] == 0.0) continue;
                 double o[3], d[3], tn, tfar;
                 if (!ray_setup(&v, cam, W, H, i, j, o, d, &tn, &tfar)) continue;
                 /* forward: the processed samples and their (alpha, colour) */

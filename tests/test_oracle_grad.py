@@ -86,6 +86,23 @@ def test_gradient_zero_where_transparent():
     assert dpar[0] == 0.0 and dpar[4] == 0.0
 
 
+def test_gradient_is_linear_in_the_upstream_gradient():
+    """Splitting dl over two disjoint ray sets splits the gradient (the sum of the two
+    equals the whole), and dl = 0 gives exactly zero: rays whose dl is zero may be
+    left unmarched."""
+    In, sp, cams, tf, pars, dl = _case(1, shading=1, et=0.99)
+    g = oracle.gmax(In, sp)
+    mask = np.zeros(dl.shape[:3], bool)
+    mask[:, ::3, ::2] = True
+    full = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, dl, gmax_value=g)
+    a = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, np.where(mask[..., None], dl, 0.0), gmax_value=g)
+    b = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, np.where(mask[..., None], 0.0, dl), gmax_value=g)
+    for x, y, z in zip(full, a, b):
+        np.testing.assert_allclose(y + z, x, rtol=1e-12, atol=1e-14 * np.abs(x).max())
+        assert np.abs(y).max() > 0 and np.abs(z).max() > 0
+    zero = oracle.render_grad(In, sp, _P(pars), tf, cams, 12, 10, np.zeros_like(dl), gmax_value=g)
+    assert all(np.all(x == 0.0) for x in zero)
+
 
 def _flat_case(In, tf_w, **over):
     dims = In.shape[::-1]
