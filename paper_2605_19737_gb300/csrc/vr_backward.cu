@@ -40,14 +40,20 @@ __device__ __forceinline__ long long bidx(const VolumeDev& v, const int b[3]) {
 }
 
 // The sample field, from the derived bricks (voxel-wise derivatives) or by the
-// per-sample stencils -- the same linear map of the voxels, either way.
-template <bool kDerived>
+// per-sample stencils -- the same linear map of the voxels, either way. kHessian:
+// the Hessian channels are read even without a curvature term (gamma = 0): the
+// forward values do not need them then, but dL/dgamma = sum dL/dw kappa / kappa_ref
+// does.
+template <bool kDerived, bool kHessian>
 __device__ __forceinline__ void eval_field(const VolumeDev& v, const TissueDev& tp, long long bi, const int i0[3], const int bc[3], int base,
                                            const float f[3], const float is[3], float fld[10]) {
     if (kDerived) {
         const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats);
         derived_channels<true, 0, 4>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld);
-        load_hessian<true>(tp, brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f, fld);
+        if (kHessian)
+            derived_channels<true, 4, 6>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld + 4);
+        else
+            load_hessian<true>(tp, brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f, fld);
     } else {
         field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
         scale_field(fld, is);
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
                 float fld[10];
-                eval_field<kDerived>(v, L.tp, bi, i0, bc, base, f, is, fld);
+                eval_field<kDerived, false>(v, L.tp, bi, i0, bc, base, f, is, fld);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 float alpha, col[3];
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
                 float fld[10];
-                eval_field<kDerived>(v, L.tp, bi, i0, bc, base, f, is, fld);
+                eval_field<kDerived, true>(v, L.tp, bi, i0, bc, base, f, is, fld);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 SampleOptics so;

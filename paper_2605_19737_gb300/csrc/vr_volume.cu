@@ -258,23 +258,52 @@ __global__ void __launch_bounds__(256) k_gmax(const float* __restrict__ I, int n
 
 // For every intensity column j of the transfer function: 1 if any row has a
 // non-zero opacity; then an exclusive prefix count, so that a brick's column
-// range can be tested in O(1). One block.
-__global__ void k_tf_alpha_prefix(const float* __restrict__ tf, int w, int h, int* __restrict__ prefix) {
+// range can be tested in O(1). One block of 1024 threads: every opacity entry is
+// read by its own thread (all loads in flight at once), each thread then owns
+// four consecutive columns of the scan (w <= 4096).
+__global__ void __launch_bounds__(1024) k_tf_alpha_prefix(const float* __restrict__ tf, int w, int h,
+                                                          int* __restrict__ prefix) {
     __shared__ int col[4096];
-    for (int j = threadIdx.x; j < w; j += blockDim.x) {
-        int any = 0;
-        for (int r = 0; r < h && !any; ++r) any = tf[4 * ((long long)r * w + j) + 3] != 0.0f;
-        col[j] = any;
+    __shared__ int warp_sum[32];
+    for (int j = threadIdx.x; j < w; j += blockDim.x) col[j] = 0;
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)w * h; e += blockDim.x)
+        if (tf[4 * e + 3] != 0.0f) col[e % w] = 1;  // racing writes all store 1
+    __syncthreads();
+    const int j0 = 4 * threadIdx.x;
+    int c[4], s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        c[q] = j0 + q < w ? col[j0 + q] : 0;
+        s += c[q];
+    }
+    // exclusive scan of the per-thread sums: within each warp, then over the warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = warp_sum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += v;
+        }
+        warp_sum[lane] = t - warp_sum[lane];  // exclusive over warps
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int j = 0; j < w; ++j) {
-            prefix[j] = run;
-            run += col[j];
-        }
-        prefix[w] = run;
+    int run = warp_sum[wid] + incl - s;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (j0 + q < w) prefix[j0 + q] = run;
+        run += c[q];
     }
+    if (j0 < w && j0 + 4 >= w) prefix[w] = run;  // the thread holding the last column
 }
 
 // A brick is empty when no transfer-function column in
@@ -414,7 +443,7 @@ cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], Vol
 
 cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
                             uint8_t* empty, int* prefix_scratch, cudaStream_t st) {
-    k_tf_alpha_prefix<<<1, 256, 0, st>>>(tf, tf_w, tf_h, prefix_scratch);
+    k_tf_alpha_prefix<<<1, 1024, 0, st>>>(tf, tf_w, tf_h, prefix_scratch);
     k_classify<<<(unsigned)((nbricks + 255) / 256), 256, 0, st>>>(grid, nbricks, prefix_scratch, tf_w, empty);
     return cudaGetLastError();
 }
