@@ -165,7 +165,9 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
 
 // 4 resident CTAs per SM (<= 128 registers): measured 1 ms faster at 1080p than
 // the 3 that the unbounded register count allows.
-template <bool kDerived>
+// kLazyHessian (derived bricks without a curvature term): a sample reads the
+// Hessian only when its opacity entry is non-zero.
+template <bool kDerived, bool kLazyHessian>
 __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
@@ -268,11 +270,28 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
                                  (i0[0] - kCells * bc[0]);
                 float fld[10];
-                eval_field<kDerived, true>(v, L.tp, bi, i0, bc, base, f, is, fld);
                 const float vval =
                     v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 SampleOptics so;
-                optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
+                if (kLazyHessian) {
+                    // I and the gradient, the table lookup, then the Hessian, which without
+                    // a curvature term only dL/dgamma needs -- and not at a zero opacity
+                    // entry (dL/dw = 0 there, and w = 1 whatever kappa)
+                    const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats);
+                    derived_channels<true, 0, 4>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld);
+                    optics_tf(fld, vval, L.tp, tf, inv_gmax, so);
+                    if (so.c.w != 0.0f) {
+                        derived_channels<true, 4, 6>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2],
+                                                     fld + 4);
+                    } else {
+#pragma unroll
+                        for (int q = 4; q < 10; ++q) fld[q] = 0.0f;
+                    }
+                    optics_rest(fld, r.dir, L.tp, so);
+                } else {
+                    eval_field<kDerived, true>(v, L.tp, bi, i0, bc, base, f, is, fld);
+                    optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
+                }
                 const float alpha = so.alpha, col[3] = {so.col[0], so.col[1], so.col[2]};
                 if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
                 const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
@@ -588,9 +607,12 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
         return cudaGetLastError();
     }
     if (L.vol.dbricks)
-        k_render_backward<true><<<grid, 128, 0, st>>>(B);
+        if (L.tp.gk == 0.0f)
+            k_render_backward<true, true><<<grid, 128, 0, st>>>(B);
+        else
+            k_render_backward<true, false><<<grid, 128, 0, st>>>(B);
     else
-        k_render_backward<false><<<grid, 128, 0, st>>>(B);
+        k_render_backward<false, false><<<grid, 128, 0, st>>>(B);
     return cudaGetLastError();
 }
 
