@@ -307,7 +307,9 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
  * d_dl_drgba = dL/dRGBA ([n_cams][H][W][4] float32, device) of the image
  * vr_render would produce for the same cameras and uniforms, writes
  *   d_dtf:     dL/d(transfer-function entries), [tf_h][tf_w][4] float32;
- *   d_dparams: dL/d(gamma, ka, kd, ks, opacity_scale), 5 float32;
+ *   d_dparams: NULL or dL/d(gamma, ka, kd, ks, opacity_scale), 5 float32 (NULL:
+ *              not computed; without a curvature term, gamma = 0, the Hessian
+ *              then enters no output and is not read);
  *   d_dvolume: NULL or dL/d(normalised voxel intensity), nx*ny*nz float32.
  * All outputs are device memory and are overwritten. I_min, I_max,
  * |grad I|_max, the vesselness volume and each ray's stopping sample are

@@ -276,16 +276,17 @@ class Context:
 
 
     def render_backward(self, vol, cams, W, H, dl_drgba, want_volume=True, skip_empty=True, dtf=None, dparams=None,
-                        dvol=None, kernel=VR_KERNEL_AUTO, packet_w=4, ray_state=None):
+                        dvol=None, kernel=VR_KERNEL_AUTO, packet_w=4, ray_state=None, want_params=True):
         """Gradients of L given dL/dRGBA (device (n, H, W, 4)): returns (dtf (h, w, 4),
-        dparams (5,) = gamma, ka, kd, ks, opacity_scale, dvolume (nz, ny, nx) or None)."""
+        dparams (5,) = gamma, ka, kd, ks, opacity_scale or None (want_params=False),
+        dvolume (nz, ny, nx) or None)."""
         torch = _torch()
         carr, n = cameras_to_c(cams)
         dev = "cuda:%d" % self.device
         tfh, tfw = self._tf_shape[vol]
         if dtf is None:
             dtf = torch.empty((tfh, tfw, 4), dtype=torch.float32, device=dev)
-        if dparams is None:
+        if dparams is None and want_params:
             dparams = torch.empty(5, dtype=torch.float32, device=dev)
         if want_volume and dvol is None:
             nx, ny, nz = self._keep[vol]
@@ -293,9 +294,9 @@ class Context:
         opts = vr_render_opts(int(kernel), int(bool(skip_empty)), int(packet_w), 4, _state_ptr(ray_state, n, W, H))
         g = dl_drgba.contiguous()
         self._check(self._lib.vr_render_backward(self._h, vol, carr, n, W, H, g.data_ptr(), dtf.data_ptr(),
-                                                 dparams.data_ptr(), dvol.data_ptr() if want_volume else None,
-                                                 ctypes.byref(opts)))
-        return dtf, dparams, (dvol if want_volume else None)
+                                                 dparams.data_ptr() if want_params else None,
+                                                 dvol.data_ptr() if want_volume else None, ctypes.byref(opts)))
+        return dtf, (dparams if want_params else None), (dvol if want_volume else None)
 
 
     def set_derived_budget(self, nbytes):

@@ -47,10 +47,11 @@ class RenderFunction(torch.autograd.Function):
         (tfc,) = fctx.saved_tensors
         vr_ctx.set_tissue_params(vol, tfc, **uniforms)  # the state the image was made with
         want_vol = fctx.has_vol and fctx.needs_input_grad[2]
+        want_par = fctx.needs_input_grad[1]  # without it (and gamma = 0) the Hessian is not read
         dtf, dpar, dvol = vr_ctx.render_backward(vol, cams, W, H, grad_img.contiguous(), want_volume=want_vol,
-                                                 ray_state=fctx.state)
+                                                 ray_state=fctx.state, want_params=want_par)
         return (dtf if fctx.needs_input_grad[0] else None,
-                dpar.to(fctx.params_device) if fctx.needs_input_grad[1] else None,
+                dpar.to(fctx.params_device) if want_par else None,
                 dvol, None, None, None, None, None, None)
 
 

@@ -815,7 +815,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: unknown id %d", vol_id);
-    if (!h_cams || !d_dl_drgba || !d_dtf || !d_dparams)
+    if (!h_cams || !d_dl_drgba || !d_dtf)
         return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: NULL pointer");
     if (n_cams < 1 || W < 1 || H < 1 || W > 16384 || H > 16384)
         return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: bad image size %d x %d x %d", n_cams, W, H);
@@ -827,7 +827,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
         return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: bad kernel choice");
     const size_t ntf = (size_t)v->tp.tf_w * v->tp.tf_h * 4;
     CK(cudaMemsetAsync(d_dtf, 0, sizeof(float) * ntf, ctx->stream), "render_backward: zero dtf");
-    CK(cudaMemsetAsync(d_dparams, 0, sizeof(float) * 5, ctx->stream), "render_backward: zero dparams");
+    if (d_dparams) CK(cudaMemsetAsync(d_dparams, 0, sizeof(float) * 5, ctx->stream), "render_backward: zero dparams");
     BackwardLaunch B;
     memset(&B, 0, sizeof B);
     fill_launch(B.r, v, W, H, skip);

@@ -165,9 +165,10 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
 
 // 4 resident CTAs per SM (<= 128 registers): measured 1 ms faster at 1080p than
 // the 3 that the unbounded register count allows.
-// kLazyHessian (derived bricks without a curvature term): a sample reads the
-// Hessian only when its opacity entry is non-zero.
-template <bool kDerived, bool kLazyHessian>
+// Derived bricks without a curvature term (gamma = 0): with kLazyHessian a sample
+// reads the Hessian only when its opacity entry is non-zero (for dL/dgamma); with
+// kNoHessian, when no uniform gradient is wanted, never.
+template <bool kDerived, bool kLazyHessian, bool kNoHessian = false>
 __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                     const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats);
                     derived_channels<true, 0, 4>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld);
                     optics_tf(fld, vval, L.tp, tf, inv_gmax, so);
-                    if (so.c.w != 0.0f) {
+                    if (!kNoHessian && so.c.w != 0.0f) {
                         derived_channels<true, 4, 6>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2],
                                                      fld + 4);
                     } else {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
 #pragma unroll
         for (int o = 16; o; o >>= 1) pv[e] += __shfl_xor_sync(0xffffffffu, pv[e], o);
     }
-    if (l == 0) {
+    if (l == 0 && B.dparams) {
 #pragma unroll
         for (int e = 0; e < 5; ++e)
             if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
 #pragma unroll
         for (int o = 16; o; o >>= 1) pv[e] += __shfl_xor_sync(0xffffffffu, pv[e], o);
     }
-    if (l == 0) {
+    if (l == 0 && B.dparams) {
 #pragma unroll
         for (int e = 0; e < 5; ++e)
             if (pv[e] != 0.0f) atomicAdd(B.dparams + e, pv[e]);
@@ -607,7 +608,9 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
         return cudaGetLastError();
     }
     if (L.vol.dbricks)
-        if (L.tp.gk == 0.0f)
+        if (L.tp.gk == 0.0f && !B.dparams)
+            k_render_backward<true, true, true><<<grid, 128, 0, st>>>(B);
+        else if (L.tp.gk == 0.0f)
             k_render_backward<true, true><<<grid, 128, 0, st>>>(B);
         else
             k_render_backward<true, false><<<grid, 128, 0, st>>>(B);

@@ -291,3 +291,20 @@ def test_backward_full_size_sampled(vr, torch, name):
     assert np.linalg.norm(dtf_o) > 0 and np.linalg.norm(dvol_o) > 0
     assert e_tf <= TOL_GRAD and e_par <= TOL_GRAD and e_vol <= TOL_GRAD
     vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("kernel", [0, 3])
+def test_uniform_gradients_optional(vr, torch, kernel):
+    """dparams = NULL: the uniforms' gradient is not computed and (gamma = 0) the
+    Hessian is not read; the transfer-function and voxel gradients are unchanged."""
+    case = _cases()["head_1d_gamma0"]
+    In32 = oracle.normalize(case["volume"]).astype(np.float32)
+    vid = _setup(vr, torch, case, In32)
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+    dl = torch.from_numpy(np.random.default_rng(76).normal(size=(n, H, W, 4)).astype(np.float32)).cuda()
+    dtf, dpar, dvol = [x.cpu().numpy() for x in vr.render_backward(vid, case["cams"], W, H, dl, kernel=kernel)]
+    dtf2, dpar2, dvol2 = vr.render_backward(vid, case["cams"], W, H, dl, kernel=kernel, want_params=False)
+    assert dpar2 is None and np.abs(dpar).max() > 0
+    np.testing.assert_allclose(dtf2.cpu().numpy(), dtf, rtol=1e-5, atol=1e-6 * np.abs(dtf).max())
+    np.testing.assert_allclose(dvol2.cpu().numpy(), dvol, rtol=1e-5, atol=1e-6 * np.abs(dvol).max())
+    vr.free_volume(vid)
