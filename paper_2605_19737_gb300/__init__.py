@@ -48,6 +48,20 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _dtype_code(data, what):
+    """VR_F32 or VR_U16 for a float32 / uint16 array or tensor (int16 tensors are read
+    as uint16); TypeError otherwise."""
+    if isinstance(data, np.ndarray):
+        dt = VR_F32 if data.dtype == np.float32 else (VR_U16 if data.dtype == np.uint16 else None)
+    else:
+        torch = _torch()
+        dt = VR_F32 if data.dtype == torch.float32 else (
+            VR_U16 if data.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)) else None)
+    if dt is None:
+        raise TypeError("%s must be float32 or uint16" % what)
+    return dt
+
+
 def _ptr(x):
     """(address, on_device) of a torch tensor or numpy array (must be contiguous)."""
     if isinstance(x, np.ndarray):
@@ -138,14 +152,7 @@ class Context:
 
     def load_volume(self, data, spacing=(1.0, 1.0, 1.0)):
         """data: (nz, ny, nx) float32 or uint16 (int16 tensors are read as uint16), host or device."""
-        if isinstance(data, np.ndarray):
-            dt = VR_F32 if data.dtype == np.float32 else (VR_U16 if data.dtype == np.uint16 else None)
-        else:
-            torch = _torch()
-            dt = VR_F32 if data.dtype == torch.float32 else (
-                VR_U16 if data.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)) else None)
-        if dt is None:
-            raise TypeError("volume must be float32 or uint16")
+        dt = _dtype_code(data, "volume")
         nz, ny, nx = data.shape
         p, dev = _ptr(data)
         vid = ctypes.c_int()
@@ -229,14 +236,7 @@ class Context:
         nx, ny, nz = self._keep[vol]
         if tuple(data.shape) != (nz, ny, nx):
             raise ValueError("second channel must have shape %s" % ((nz, ny, nx),))
-        if isinstance(data, np.ndarray):
-            dt = VR_F32 if data.dtype == np.float32 else (VR_U16 if data.dtype == np.uint16 else None)
-        else:
-            torch = _torch()
-            dt = VR_F32 if data.dtype == torch.float32 else (
-                VR_U16 if data.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)) else None)
-        if dt is None:
-            raise TypeError("channel must be float32 or uint16")
+        dt = _dtype_code(data, "channel")
         p, dev = _ptr(data)
         self._check(self._lib.vr_load_second_channel(self._h, vol, p, int(dev), dt))
 

@@ -197,6 +197,17 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Device address of caller data: the data itself (on_device), or a copy of the host
+// data in the context's staging buffer, enqueued on the context's stream.
+cudaError_t device_input(vr_ctx* ctx, const void* data, int on_device, size_t bytes, const void** raw) {
+    *raw = data;
+    if (on_device) return cudaSuccess;
+    cudaError_t e = ensure_stage(ctx, bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_stage, data, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) *raw = ctx->d_stage;
+    return e;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -383,11 +394,7 @@ vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype 
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_vc, 0, sizeof(VolConst), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->d_empty, 0, v->nbricks, ctx->stream);
     const void* raw = data;
-    if (e == cudaSuccess && !on_device) {
-        e = ensure_stage(ctx, esz * v->nvox);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->d_stage, data, esz * v->nvox, cudaMemcpyHostToDevice, ctx->stream);
-        raw = ctx->d_stage;
-    }
+    if (e == cudaSuccess) e = device_input(ctx, data, on_device, esz * v->nvox, &raw);
     if (e != cudaSuccess) {
         free_volume(ctx, v);
         return cuda_fail(ctx, e, "load_volume: allocate/copy");
@@ -617,12 +624,7 @@ vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int 
     if (!v->d_ch2) CK(dalloc(ctx, &v->d_ch2, sizeof(float) * 8), "load_second_channel: normalisation constants");
     const size_t esz = dtype == VR_F32 ? 4 : 2;
     const void* raw = data;
-    if (!on_device) {
-        CK(ensure_stage(ctx, esz * v->nvox), "load_second_channel: staging buffer");
-        CK(cudaMemcpyAsync(ctx->d_stage, data, esz * v->nvox, cudaMemcpyHostToDevice, ctx->stream),
-           "load_second_channel: copy");
-        raw = ctx->d_stage;
-    }
+    CK(device_input(ctx, data, on_device, esz * v->nvox, &raw), "load_second_channel: copy");
     // Eq. 1 applied to the channel itself: its own I_min, I_max
     vr_status st = vr_reduce_minmax(ctx, raw, dtype, v->nvox, v->d_ch2);
     if (st != VR_OK) return st;
