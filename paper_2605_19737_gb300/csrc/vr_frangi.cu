@@ -238,11 +238,14 @@ __global__ void __launch_bounds__(256) k_frangi_v(const float* __restrict__ sm, 
     if (c > 0.0f && H[0] + H[1] + H[2] < 0.0f) {
         eig3_sorted(H, l);
         if (!(l[1] > 0.0f || l[2] > 0.0f || l[1] == 0.0f || l[2] == 0.0f)) {
-            const float Ra = fabsf(l[1]) / fabsf(l[2]);
-            const float Rb = fabsf(l[0]) / sqrtf(fabsf(l[1] * l[2]));
+            // fast reciprocal, reciprocal square root and exponential: a few ulp on
+            // factors in [0, 1], far inside the 1e-4 the response is held to
+            const float Ra = __fdividef(fabsf(l[1]), fabsf(l[2]));
+            const float Rb = fabsf(l[0]) * rsqrtf(fabsf(l[1] * l[2]));
             const float S = hessian_norm(H);
             // alpha = beta = 0.5: 2 alpha^2 = 2 beta^2 = 0.5
-            v = (1.0f - expf(-Ra * Ra / 0.5f)) * expf(-Rb * Rb / 0.5f) * (1.0f - expf(-(S * S) / (2.0f * c * c)));
+            v = (1.0f - __expf(-2.0f * Ra * Ra)) * __expf(-2.0f * Rb * Rb) *
+                (1.0f - __expf(-(S * S) * __fdividef(0.5f, c * c)));
         }
     }
     V[idx] = fmaxf(V[idx], v);

@@ -145,7 +145,10 @@ __global__ void __launch_bounds__(256) k_make_bricks(const float* __restrict__ n
     const long long b = blockIdx.x;
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
     float* dst = bricks + b * kBrickVox;
-    for (int e = threadIdx.x; e < kBrickVox; e += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < (kBrickVox + 255) / 256; ++q) {  // 256 threads: the loads issue back to back
+        const int e = threadIdx.x + 256 * q;
+        if (e >= kBrickVox) break;
         const int lx = e % kEdge, ly = (e / kEdge) % kEdge, lz = e / (kEdge * kEdge);
         const int x = min(max(kCells * bx - 1 + lx, 0), nx - 1);
         const int y = min(max(kCells * by - 1 + ly, 0), ny - 1);
@@ -167,7 +170,10 @@ __global__ void __launch_bounds__(256) k_make_derived(const float* __restrict__ 
     const long long b = blockIdx.x;
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
     const int x0 = kCells * bx - 1, y0 = kCells * by - 1, z0 = kCells * bz - 1;
-    for (int e = threadIdx.x; e < kT * kT * kT; e += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < (kT * kT * kT + 255) / 256; ++q) {  // 256 threads: the loads issue back to back
+        const int e = threadIdx.x + 256 * q;
+        if (e >= kT * kT * kT) break;
         const int tx = e % kT, ty = (e / kT) % kT, tz = e / (kT * kT);
         const int x = min(max(x0 + tx, 0), nx - 1), y = min(max(y0 + ty, 0), ny - 1), z = min(max(z0 + tz, 0), nz - 1);
         tile[e] = __ldg(norm + ((long long)z * ny + y) * nx + x);
