@@ -25,15 +25,20 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="brainweb_1080p",
-                    choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam", "vessel_1080p"])
+                    choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam", "vessel_1080p",
+                             "batched"])
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=4)
     ap.add_argument("--warps", type=int, default=4)
     ap.add_argument("--backward", action="store_true", help="also run the adjoint raymarch after each frame")
+    ap.add_argument("--cams-per-volume", type=int, default=8,
+                    help="batched: orbit cameras per volume (the benchmark uses 64)")
     ap.add_argument("--precompute-reps", type=int, default=1,
                     help="run the morphology precompute this many times (timed with CUDA events)")
     args = ap.parse_args()
+    if args.workload == "batched":
+        return run_batched(args)
     if args.workload == "head64":
         case = workloads.head64_128px()
     elif args.workload == "diff_head128_8cam":
@@ -80,6 +85,41 @@ def main():
     print("%s %s: %.3f ms/frame (mean of %d)" % (args.workload, args.kernel, float(np.mean(ts)), len(ts)))
     if args.backward:
         print("%s %s backward: %.3f ms/frame" % (args.workload, args.kernel, float(np.mean(tb))))
+
+
+def run_batched(args):
+    """The benchmark's batched workload (4 uneven volumes, 512x512 views) with fewer
+    cameras per volume, rendered by the persistent batch kernel (4x8 packets, 4 warps
+    per CTA: the autotuned shape) --frames times."""
+    import torch
+
+    import paper_2605_19737_gb300 as pkg
+    from phantoms import workloads
+
+    cases = workloads.batched_4vol_64cam(n_cams=args.cams_per_volume)
+    with pkg.Context(0) as ctx:
+        vids, views = [], []
+        for case in cases:
+            vid = ctx.load_volume(torch.from_numpy(case["volume"]).cuda(), case["spacing"])
+            ctx.precompute_morphology(vid)
+            ctx.set_tissue_params(vid, case["tf"], **case["params"])
+            vids.append(vid)
+            for c in range(case["cams"].shape[0]):
+                views.append((vid, case["cams"][c], torch.empty((case["H"], case["W"], 4), device="cuda"),
+                              case["W"], case["H"]))
+        bid = ctx.batch_create(views)
+        ts = []
+        for _ in range(args.frames):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            ctx.batch_render(bid, packet_w=4, warps_per_block=4)
+            e.record()
+            ctx.synchronize()
+            ts.append(s.elapsed_time(e))
+        ctx.batch_free(bid)
+        for vid in vids:
+            ctx.free_volume(vid)
+    print("batched %d views: %.3f ms/batch (mean of %d)" % (len(views), float(np.mean(ts)), len(ts)))
 
 
 if __name__ == "__main__":
