@@ -308,3 +308,31 @@ def test_uniform_gradients_optional(vr, torch, kernel):
     np.testing.assert_allclose(dtf2.cpu().numpy(), dtf, rtol=1e-5, atol=1e-6 * np.abs(dtf).max())
     np.testing.assert_allclose(dvol2.cpu().numpy(), dvol, rtol=1e-5, atol=1e-6 * np.abs(dvol).max())
     vr.free_volume(vid)
+
+
+def test_fit_checkpoint_resume_on_gpu(vr, torch, tmp_path):
+    """The transfer-function fit through the C ABI, interrupted after a checkpoint and
+    resumed from it, ends where the uninterrupted fit ends (float atomics in the
+    backward make each run's gradients differ in the last bits, so within rounding)."""
+    from paper_2605_19737_gb300 import autograd as ag
+    from paper_2605_19737_gb300.fit import fit_transfer_function
+    case = _cases()["head_1d"]
+    In32 = oracle.normalize(case["volume"]).astype(np.float32)
+    vid = _setup(vr, torch, case, In32)
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+    fixed = {k: v for k, v in case["params"].items() if k not in ag.PARAM_NAMES}
+    params = torch.tensor([case["params"][k] for k in ag.PARAM_NAMES], dtype=torch.float32)
+    tf_target = np.clip(case["tf"] + np.random.default_rng(77).normal(0, 0.05, case["tf"].shape), 0, 1)
+    with torch.no_grad():
+        target = ag.render(vr, vid, torch.from_numpy(tf_target.astype(np.float32)).cuda(), params, case["cams"], W,
+                           H, fixed)
+    tf0 = torch.from_numpy(case["tf"]).cuda()
+    ref_tf, ref_losses, _ = fit_transfer_function(vr, vid, case["cams"], W, H, tf0, target, fixed, params, steps=12)
+    ck = str(tmp_path / "fit.pt")
+    fit_transfer_function(vr, vid, case["cams"], W, H, tf0, target, fixed, params, steps=8, checkpoint=ck, every=4)
+    tf, losses, _ = fit_transfer_function(vr, vid, case["cams"], W, H, tf0, target, fixed, params, steps=12,
+                                          checkpoint=ck, every=4)
+    assert len(losses) == 12 and losses[-1] < losses[0]
+    np.testing.assert_allclose(losses, ref_losses, rtol=1e-4)
+    np.testing.assert_allclose(tf.cpu().numpy(), ref_tf.cpu().numpy(), rtol=0, atol=1e-4)
+    vr.free_volume(vid)
