@@ -1,6 +1,6 @@
 """Edge cases of the raymarch through the C ABI, each against the FP64 oracle:
 the smallest volume (2^3: one cell, one brick), an axis of the maximum length
-(2048), 1x1 and one-row images, an eye inside the volume (t_near clamped to 0),
+(2048), 1x1 and one-row images, the widest and tallest images (16384), an eye inside the volume (t_near clamped to 0),
 cameras that miss the volume, and more cameras than one launch takes (chunked)."""
 
 import numpy as np
@@ -110,3 +110,16 @@ def test_more_cameras_than_one_launch(vr, torch):
         x = x.cpu().numpy()
         assert np.linalg.norm(a - x) <= 1e-5 * np.linalg.norm(x)
     vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_maximum_image_width(vr, torch, kernel):
+    """The widest image the ABI accepts (16384 pixels) and a one-pixel-wide column
+    of the largest height, against the oracle."""
+    case = workloads.head64_128px()
+    dims = case["volume"].shape[::-1]
+    for W, H in ((16384, 3), (1, 16384)):
+        cams = [ph.orbit_camera(dims, (1, 1, 1), 30, 20, width=W, height=H, distance_factor=1.6)]
+        c = dict(case, cams=ph.camera_array(cams), W=W, H=H)
+        img, res = _render_and_compare(vr, torch, c, kernel, "%dx%d" % (W, H))
+        assert res.rgba[..., 3].max() > 0.0
