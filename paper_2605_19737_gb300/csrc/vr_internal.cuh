@@ -14,6 +14,7 @@
 
 #include "vr.h"
 #include "vr_async.cuh"
+#include "vr_df.cuh"
 
 namespace vr {
 
@@ -79,21 +80,24 @@ struct VolumeDev {
     const VolConst* vc;
 };
 
-// Per-launch constants of the ray setup, computed once on the host in FP64.
+// Per-launch constants of the ray setup, computed once on the host in FP64 and
+// passed as double-floats (hi + lo).
 struct RayConsts {
-    double two_over_w, two_over_h;  // 2/W, 2/H
-    double inv_s[3];                // 1/spacing
-    double dt, inv_dt;              // sample spacing step_vox * min(s) and its inverse
+    dfloat_h two_over_w, two_over_h;  // 2/W, 2/H
+    dfloat_h inv_s[3];                // 1/spacing
+    dfloat_h dt;                      // sample spacing step_vox * min(s)
+    float inv_dt;                     // 1/dt (only for the sample-count estimate)
 };
 
 inline RayConsts make_ray_consts(int W, int H, const float s[3], float step_vox) {
     RayConsts c;
-    c.two_over_w = 2.0 / (double)W;
-    c.two_over_h = 2.0 / (double)H;
-    for (int q = 0; q < 3; ++q) c.inv_s[q] = 1.0 / (double)s[q];
+    c.two_over_w = df_split(2.0 / (double)W);
+    c.two_over_h = df_split(2.0 / (double)H);
+    for (int q = 0; q < 3; ++q) c.inv_s[q] = df_split(1.0 / (double)s[q]);
     const float smin = s[0] < s[1] ? (s[0] < s[2] ? s[0] : s[2]) : (s[1] < s[2] ? s[1] : s[2]);
-    c.dt = (double)step_vox * (double)smin;
-    c.inv_dt = 1.0 / c.dt;
+    const double dt = (double)step_vox * (double)smin;
+    c.dt = df_split(dt);
+    c.inv_dt = (float)(1.0 / dt);
     return c;
 }
 

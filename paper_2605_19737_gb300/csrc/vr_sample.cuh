@@ -31,59 +31,62 @@ struct RayDev {
     float dir[3];     // unit ray direction
 };
 
-// Ray through pixel (i, j) in FP64: direction normalize(fwd + a right + b up),
+// Ray through pixel (i, j): direction normalize(fwd + a right + b up),
 // a = 2(i+1/2)/W - 1, b = 1 - 2(j+1/2)/H; slab intersection with the volume box;
-// t_near = max(t0, 0); ns = #{k : t_near + (k+1/2) dt < t_far}. Divisions are
-// limited to one reciprocal of the length and one per direction component
-// (FP64 division is a long instruction sequence on this part). Returns false
-// when the ray misses the box or has no sample.
+// t_near = max(t0, 0); ns = #{k : t_near + (k+1/2) dt < t_far}. Computed in
+// double-float arithmetic (~48 bits, vr_df.cuh): FP64 is a small fraction of the
+// FP32 rate on this part and its registers come in pairs. Returns false when the
+// ray misses the box or has no sample.
 __device__ __forceinline__ bool setup_ray(const CamDev& c, const RayConsts& rc, int i, int j, const int n[3],
                                           const float s[3], RayDev& r) {
-    const double a = fma((double)i + 0.5, rc.two_over_w, -1.0);
-    const double b = fma(-((double)j + 0.5), rc.two_over_h, 1.0);
-    double d[3], o[3];
+    // i + 1/2 and j + 1/2 are exact in float for image sizes up to 2^22
+    const dfloat tw = {rc.two_over_w.hi, rc.two_over_w.lo}, th = {rc.two_over_h.hi, rc.two_over_h.lo};
+    const dfloat a = df_add_f(df_mul_f(tw, (float)i + 0.5f), -1.0f);
+    const dfloat b = df_add_f(df_neg(df_mul_f(th, (float)j + 0.5f)), 1.0f);
+    dfloat d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d[q] = df_add(df_add_f(df_mul_f(a, c.right[q]), c.fwd[q]), df_mul_f(b, c.up[q]));
+    const dfloat inv_len = df_rsqrt(df_add(df_add(df_mul(d[0], d[0]), df_mul(d[1], d[1])), df_mul(d[2], d[2])));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) d[q] = df_mul(d[q], inv_len);
+    dfloat t0 = {-INFINITY, 0.0f}, t1 = {INFINITY, 0.0f};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        o[q] = (double)c.eye[q];
-        d[q] = fma(b, (double)c.up[q], fma(a, (double)c.right[q], (double)c.fwd[q]));
-    }
-    const double inv_len = 1.0 / sqrt(fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2])));
-#pragma unroll
-    for (int q = 0; q < 3; ++q) d[q] *= inv_len;
-    double t0 = -INFINITY, t1 = INFINITY;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const double hi = (double)n[q] * (double)s[q];
-        if (d[q] == 0.0) {
-            if (o[q] < 0.0 || o[q] > hi) return false;
+        const float o = c.eye[q];
+        const dfloat hi = df_two_prod((float)n[q], s[q]);  // exact
+        if (d[q].hi == 0.0f) {
+            if (o < 0.0f || df_lt(hi, dfloat{o, 0.0f})) return false;
             continue;
         }
-        const double inv_d = 1.0 / d[q];
-        const double ta = -o[q] * inv_d;
-        const double tb = (hi - o[q]) * inv_d;
-        const double lo_t = ta < tb ? ta : tb, hi_t = ta < tb ? tb : ta;
-        if (lo_t > t0) t0 = lo_t;
-        if (hi_t < t1) t1 = hi_t;
+        const dfloat inv_d = df_recip(d[q]);
+        const dfloat ta = df_mul_f(inv_d, -o);
+        const dfloat tb = df_mul(df_add_f(hi, -o), inv_d);
+        const bool ord = df_lt(ta, tb);
+        const dfloat lo_t = ord ? ta : tb, hi_t = ord ? tb : ta;
+        if (df_lt(t0, lo_t)) t0 = lo_t;
+        if (df_lt(hi_t, t1)) t1 = hi_t;
     }
-    const double tn = t0 > 0.0 ? t0 : 0.0, tf = t1;
-    if (!(tn < tf)) return false;
-    const double dt = rc.dt;
+    const dfloat tn = df_lt(dfloat{0.0f, 0.0f}, t0) ? t0 : dfloat{0.0f, 0.0f}, tf = t1;
+    if (!df_lt(tn, tf)) return false;
+    const dfloat dt = {rc.dt.hi, rc.dt.lo};
     // estimate, then settle on the exact predicate t_near + (k + 1/2) dt < t_far
-    long long ns = (long long)ceil(fma(tf - tn, rc.inv_dt, -0.5));
-    if (ns < 0) ns = 0;
-    while (ns > 0 && !(fma((double)(ns - 1) + 0.5, dt, tn) < tf)) --ns;
-    while (fma((double)ns + 0.5, dt, tn) < tf) ++ns;
+    auto before_far = [&](int k) { return df_lt(df_add(tn, df_mul_f(dt, (float)k + 0.5f)), tf); };
+    const float est = ceilf(fmaf(__fsub_rn(tf.hi, tn.hi), rc.inv_dt, -0.5f));
+    int ns = est > 0.0f ? (est < 4194304.0f ? (int)est : 4194304) : 0;
+    while (ns > 0 && !before_far(ns - 1)) --ns;
+    while (before_far(ns)) ++ns;
     if (ns == 0) return false;
-    r.ns = (int)ns;
+    r.ns = ns;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double un = fma(fma(tn, d[q], o[q]), rc.inv_s[q], -0.5);
-        r.uhi[q] = (float)un;
-        r.ulo[q] = (float)(un - (double)r.uhi[q]);
-        const double st = dt * d[q] * rc.inv_s[q];
-        r.dhi[q] = (float)st;
-        r.dlo[q] = (float)(st - (double)r.dhi[q]);
-        r.dir[q] = (float)d[q];
+        const dfloat is = {rc.inv_s[q].hi, rc.inv_s[q].lo};
+        const dfloat un = df_add_f(df_mul(df_add_f(df_mul(tn, d[q]), c.eye[q]), is), -0.5f);
+        r.uhi[q] = un.hi;
+        r.ulo[q] = un.lo;
+        const dfloat st = df_mul(df_mul(dt, d[q]), is);
+        r.dhi[q] = st.hi;
+        r.dlo[q] = st.lo;
+        r.dir[q] = d[q].hi;
     }
     return true;
 }
