@@ -194,13 +194,15 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
 
     RayDev r;
     const bool hit = inside && setup_ray(L.cams[cam], L.rc, i, j, v.n, v.s, r);
+    float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int kstop = -1;  // the ray's last sample (-1: none)
+    float Tk = 1.0f;
     if (hit) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
-        const float4 g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
+        g4 = __ldg(reinterpret_cast<const float4*>(B.dl_drgba) + pix);
         // 1. the ray's last sample and the transmittance in front of it: recorded by the
         // forward render (ray_state), or re-marched forward here
-        int kstop = r.ns - 1;
-        float Tk;
+        kstop = r.ns - 1;
         if (L.ray_state) {
             const float2 st = __ldg(L.ray_state + pix);
             kstop = __float_as_int(st.x);
@@ -248,11 +250,16 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
             // transmittance before the stopping sample (1 when no sample had opacity)
             Tk = (klast == kstop) ? 1.0f - A_prev : 1.0f - A;
         }
-        {
+    }
+    {
             float Tk1 = Tk, R0 = 0.f, R1 = 0.f, R2 = 0.f, P = 1.0f;
             const float dC[3] = {g4.x, g4.y, g4.z};
-            // 2. reverse sweep
-            for (int kr = kstop; kr >= 0; --kr) {
+            // 2. reverse sweep, the lanes of a warp in step: at iteration kr every lane
+            // whose ray reaches that far works on its sample kr, so neighbouring rays sit
+            // at nearly the same depth and their reads and reductions hit the same cells
+            const int kmax = __reduce_max_sync(0xffffffffu, kstop);
+            for (int kr = kmax; kr >= 0; --kr) {
+                if (kr > kstop) continue;
                 const float kk = (float)kr + 0.5f;
                 int i0[3], bc[3];
                 float f[3];
@@ -337,7 +344,6 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                 P *= (1.0f - alpha);
                 Tk1 = Tk;
             }
-        }
     }
     sink.flush();
     // uniform gradients: warp sums, one atomic per warp and parameter
