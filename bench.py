@@ -16,8 +16,9 @@ Also reported (not timed in the step): fps_wall (vr_render wall clock, launch
 included), fwd+bwd on the same 1080p view, fwd+bwd over the 8 views of the
 differentiable 128^3 workload, the batched persistent render (4 volumes x 64
 cameras, CUDA graph), the vesselness precompute, time to first pixel, and the
-roofline of the forward kernel against a measured FP32 FMA peak. --fit adds the
-200-step transfer-function fit. Run `python bench.py --impl reference` for the
+roofline of the forward kernel against a measured FP32 FMA peak, the 1080p render
+of the vessel volume through its (I, V) table, the 64^3 head at 128x128, and the
+200-step transfer-function fit (--no-fit skips it). Run `python bench.py --impl reference` for the
 FP64 CPU oracle on the same workload (a bounded sample of the frame).
 """
 
@@ -37,7 +38,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Gsamples/s & FPS at 1080p (fwd, fwd+bwd) vs plain fwd, % of HBM roofline"
 UNIT = "Gsamples/s"
 L2_FLUSH_BYTES = 256 << 20
-# FP32 operations per sample of the raymarch, counted from the algorithm.
+# FP32 operations per sample of the raymarch.
+# The survey's per-unit figure for the method (per-sample trilinear I, gradient and
+# Hessian, curvature, Eq. 4, shading, Eqs. 5-6): ~400 FP32 FLOP per evaluated sample.
+# This is what `roofline.achieved` counts.
+FLOPS_PER_SAMPLE_SURVEY = 400
+# The count of the arithmetic this implementation does, from the algorithm.
 # Derived bricks (voxel-wise I, gradient, Hessian), in two stages:
 #   every interpolated sample (evaluated, and not in a cell classified empty):
 #   position (18), trilinear weights (19), 8 corners x
@@ -51,9 +57,6 @@ L2_FLUSH_BYTES = 256 << 20
 # (15) in place of the 179 of the derived interpolation: 124 + 383 = 507.
 FLOPS_STAGE1 = {"gather": 148, "stencil": 0, "staged": 0}
 FLOPS_SHADED = {"gather": 155, "stencil": 507, "staged": 507}
-# Bytes of one brick: derived (9^3 corners x 12 float32) or intensity (12^3 float32).
-BRICK_BYTES = {"gather": 9 * 9 * 9 * 12 * 4, "stencil": 12 ** 3 * 4, "staged": 12 ** 3 * 4}
-DERIVED_BUDGET_BYTES = 16 << 30
 KERNEL_SOURCES = ("paper_2605_19737_gb300/csrc/vr_render.cu", "paper_2605_19737_gb300/csrc/vr_march.cuh",
                   "paper_2605_19737_gb300/csrc/vr_sample.cuh", "paper_2605_19737_gb300/csrc/vr_internal.cuh")
 
@@ -166,10 +169,10 @@ def cpu_baseline(case, stride, threads=None, min_seconds=0.0):
 
 
 def workload_config(args, ws):
-    """The benchmark workload, as both arms report it."""
+    """The benchmark workload, as both arms report it (the same object in both)."""
     return {"workload": "brainweb_1080p", "volume": "181x217x181 u16 (BrainWeb-shaped phantom)",
             "image": "1920x1080", "tf": "2D 256x64 (I, |g|/gmax), Table 2 windows", "step_vox": 0.5,
-            "kernel": args.kernel, "l2": "flushed between frames (256 MB write)",
+            "l2": "flushed between frames (256 MB write)",
             "parallelism": "replicas" if ws > 1 else "single"}
 
 
@@ -193,7 +196,7 @@ def run_reference(args):
     _json_line({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * last["seconds"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": dict(workload_config(args, 1), sample=cb["sample"]),
+                "data": "synthetic", "config": workload_config(args, args.gpus),
                 "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}})
 
@@ -239,6 +242,34 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
             "dense_samples": dense, "fwd_ms": f_ms, "bwd_ms": b_ms,
             "fwd_gsamples_per_s": dense / (f_ms * 1e-3) / 1e9,
             "fwd_bwd_gsamples_per_s": dense / ((f_ms + b_ms) * 1e-3) / 1e9}
+
+
+def timed_view(ctx, vid, case, flush, args, kernel, label):
+    """Forward render of one named workload's views: CUDA-event time per frame (L2
+    flushed between frames), dense-equivalent Gsamples/s and FPS."""
+    import torch
+
+    import paper_2605_19737_gb300 as pkg
+    dev = flush.device
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+    out = torch.empty((n, H, W, 4), device=dev)
+    ctr = pkg.new_counters(dev.index or 0)
+    ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, counters=ctr)
+    torch.cuda.synchronize()
+    c = [int(x) for x in ctr.cpu().numpy()[:6]]
+    ts = []
+    for i in range(args.warmup + max(5, min(20, args.steps))):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel)
+        e.record()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ts.append(s.elapsed_time(e))
+    ms = float(np.mean(ts))
+    return {"workload": label, "ms_per_frame": ms, "fps": 1000.0 * n / ms, "dense_samples": c[1],
+            "evaluated_samples": c[2], "gsamples_per_s": c[1] / (ms * 1e-3) / 1e9}
 
 
 def run_batched(args, ctx, dev, flush):
@@ -444,11 +475,11 @@ def run(args):
                            "its reverse sweeps there; bwd_ms_re_march: the backward re-marching each ray instead",
                    "plain_fwd_gsamples_per_s": value}
 
-    # Per-volume vesselness precompute (sigma 1, 2, 3) on the 256x256x176 vessel phantom.
-    precompute = None
+    # Per-volume vesselness precompute (sigma 1, 2, 3) on the 256x256x176 vessel phantom,
+    # then the 1080p render of that volume through its (I, V) transfer function.
+    precompute = vessel = head64 = None
     if not args.no_batch:
-        from phantoms import workloads as wl
-        vcase = wl.vessel_1080p()
+        vcase = workloads.vessel_1080p()
         vvid = ctx.load_volume(torch.from_numpy(vcase["volume"]).to(dev), vcase["spacing"])
         pre = []
         for _ in range(4):
@@ -458,32 +489,47 @@ def run(args):
             s1.record()
             torch.cuda.synchronize()
             pre.append(s0.elapsed_time(s1))
-        ctx.free_volume(vvid)
         precompute = {"workload": "vessel 256x256x176 float32, Frangi sigma 1, 2, 3 + |grad I|max",
                       "ms": float(np.median(pre[1:]))}
+        ctx.set_tissue_params(vvid, vcase["tf"], **vcase["params"])
+        vessel = timed_view(ctx, vvid, vcase, flush, args, kernel,
+                            "vessel_1080p: 256x256x176 float32 vessel tree, 2D TF over (I, V), Phong, 1920x1080")
+        ctx.free_volume(vvid)
+        hcase = workloads.head64_128px()
+        hvid = ctx.load_volume(torch.from_numpy(hcase["volume"]).to(dev), hcase["spacing"])
+        ctx.precompute_morphology(hvid)
+        ctx.set_tissue_params(hvid, hcase["tf"], **hcase["params"])
+        head64 = timed_view(ctx, hvid, hcase, flush, args, kernel,
+                            "head64_128px: 64^3 float32 head, 1D TF, Phong, 128x128")
+        ctx.free_volume(hvid)
 
     batched = None if args.no_batch else run_batched(args, ctx, dev, flush)
     multiview = None if args.no_backward else fwd_bwd_multiview(ctx, dev, flush, args)
     fit = None
-    if args.fit and ws == 1:
+    if not args.no_fit and ws == 1:
         from paper_2605_19737_gb300 import fit as fitmod
         fit = fitmod.run(steps=200)
     hbm, smax, peak_kind = _peaks()
-    nbricks = int(np.prod([(n - 1 + 7) // 8 for n in vol_np.shape]))
     kind = args.kernel
-    if kind == "gather" and nbricks * BRICK_BYTES["gather"] > DERIVED_BUDGET_BYTES:
+    nbricks, _, derived_bytes = ctx.get_layout(vid)
+    if kind == "gather" and derived_bytes == 0:
         kind = "stencil"  # derived bricks are not built above the memory budget
-    # unique bytes a frame must move at least: the bricks it reads (bounded by the
-    # whole brick store) plus the RGBA float32 image it writes
-    frame_bytes = nbricks * BRICK_BYTES[kind] + W * H * 16
+    # algorithmic bytes of a frame: the voxels at their stored dtype (u16; every voxel
+    # once, an upper bound of what a frame touches) plus the RGBA float32 image it writes
+    vox_bytes = int(vol_np.size * vol_np.dtype.itemsize)
+    frame_bytes = vox_bytes + W * H * 16
+    traffic = measured_traffic()
+    props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or smax
-    fp32_nominal = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp32_nominal = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     fma_ms, fma_flops = ctx.fma_peak()
     fp32_peak = fma_flops / 1e12
-    # algorithmic: the method's per-sample arithmetic for every evaluated sample (the
-    # unit of the target design: samples outside empty bricks); executed: what the
-    # kernel ran after its exact skips (empty cells, zero-opacity samples)
-    frame_flops = evald * (FLOPS_STAGE1[kind] + FLOPS_SHADED[kind])
+    # algorithmic: the survey's per-sample figure for the method times every evaluated
+    # sample (the samples outside empty bricks); builder count: this implementation's
+    # own per-sample arithmetic; executed: what the kernel ran after its exact skips
+    # (empty cells, zero-opacity samples)
+    frame_flops = evald * FLOPS_PER_SAMPLE_SURVEY
+    builder_flops = evald * (FLOPS_STAGE1[kind] + FLOPS_SHADED[kind])
     executed_flops = interp * FLOPS_STAGE1[kind] + shaded * FLOPS_SHADED[kind]
     achieved_tflops = frame_flops / (ms * 1e-3) / 1e12
     if rank == 0:
@@ -499,27 +545,37 @@ def run(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, ws),
+            "config": workload_config(args, ws), "kernel": args.kernel,
             "fps": 1000.0 / ms, "fps_wall": fps_wall,
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "interpolated_per_frame": interp,
                         "shaded_per_frame": shaded, "rays": rays},
             "ttfp_ms": ttfp_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "flops_per_evaluated_sample": FLOPS_STAGE1[kind] + FLOPS_SHADED[kind],
+                         "frac": achieved_tflops / fp32_peak, "traffic": traffic,
+                         "flops_per_evaluated_sample": FLOPS_PER_SAMPLE_SURVEY,
                          "algorithmic_flops_per_frame": frame_flops,
+                         "builder_flops_per_evaluated_sample": FLOPS_STAGE1[kind] + FLOPS_SHADED[kind],
+                         "frac_builder_count": builder_flops / (ms * 1e-3) / 1e12 / fp32_peak,
                          "executed_flops_per_frame": executed_flops,
                          "executed_tflops": executed_flops / (ms * 1e-3) / 1e12,
-                         "frac": achieved_tflops / fp32_peak, "traffic": measured_traffic(),
+                         "frac_executed": executed_flops / (ms * 1e-3) / 1e12 / fp32_peak,
                          "peak_source": "measured: FP32 FMA probe vr_fma_peak (8 independent chains per thread, "
-                                        "%.3f ms per launch); nominal 152 SMs x 128 lanes x 2 x %.0f MHz = %.1f"
-                                        % (fma_ms, sm_mhz, fp32_nominal)},
+                                        "%.3f ms per launch); nominal %d SMs x 128 lanes x 2 x %.0f MHz = %.1f"
+                                        % (fma_ms, props.multi_processor_count, sm_mhz, fp32_nominal)},
             "hbm_roofline": {"achieved": frame_bytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                              "frac": frame_bytes / (ms * 1e-3) / 1e9 / hbm, "frac_vs_8tbs":
                              frame_bytes / (ms * 1e-3) / 1e9 / 8000.0, "bytes_per_frame": frame_bytes,
+                             "bytes": "algorithmic: %d voxels x %d B (u16, each once) + %dx%d RGBA float32 image"
+                                      % (vol_np.size, vol_np.dtype.itemsize, W, H),
+                             "layout_bytes_derived_store": derived_bytes, "bricks": nbricks,
+                             "measured_dram_bytes_per_launch": traffic,
+                             "measured_over_algorithmic": (traffic / frame_bytes) if traffic else None,
                              "peak_source": peak_kind},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tf_host.numel() * 4 + 48),
                     "d2h_bytes_per_step": int(W * H * 16), "ms_per_step": 1000.0 * e2e_s},
             "fwd_bwd": fwd_bwd,
+            "vessel_1080p": vessel,
+            "head64": head64,
             "batched": batched,
             "fwd_bwd_multiview": multiview,
             "precompute": precompute,
@@ -543,7 +599,7 @@ def main():
     ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--fit", action="store_true", help="also run the 200-step transfer-function fit")
+    ap.add_argument("--no-fit", action="store_true", help="skip the 200-step transfer-function fit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

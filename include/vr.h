@@ -241,6 +241,15 @@ vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm);
  *   h_nb: 3 ints (nbx, nby, nbz). Any of them may be NULL. */
 vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb);
 
+/* Storage layout of a volume (no GPU work; any pointer may be NULL):
+ *   nbricks:       bricks of 8^3 interpolation cells, nbx*nby*nbz;
+ *   brick_bytes:   the intensity brick store (12^3 float32 per brick);
+ *   derived_bytes: the derived-brick store of the voxel-wise derivatives built by
+ *                  vr_precompute_morphology (0 when it is not built).
+ * Errors: INVALID_ARG (unknown volume). */
+vr_status vr_get_layout(vr_ctx* ctx, int vol_id, long long* nbricks, unsigned long long* brick_bytes,
+                        unsigned long long* derived_bytes);
+
 /* Copy the second channel -- the vesselness volume, or the normalised channel of
  * vr_load_second_channel -- (nx*ny*nz float32) to `out` (device if
  * out_on_device, else host; synchronises for host). NOT_READY without it. */
@@ -348,7 +357,11 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
  *            current CUDA device;
  *   h_msg/msg_len: NULL or a host buffer that receives a message on failure.
  * The first call on a device looks up the static array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The
+ * address is kept per device together with the id of the CUDA context it was
+ * taken in: after the context is destroyed and re-created (cudaDeviceReset), the
+ * next call sees the new context and looks the address up again, so that call
+ * too should come before any capture.
  * All calls share the one array per device, so calls that overlap on the GPU
  * (e.g. on two streams) race; every call rewrites all the entries it reads.
  * Errors: INVALID_ARG (NULL pointers, nbricks outside [1, 2^31], tf_w outside

@@ -274,13 +274,55 @@ void or_tf_sample(const double *tf, int w, int h, double x, double y, double *rg
 /* Distance of x to the nearest integer. */
 static double frac_dist(double x) { return fabs(x - floor(x + 0.5)); }
 
+/* Largest magnitudes over the 8 corners of the cell that field_at interpolates at p:
+ * intensity M, gradient norm G, Hessian entry Hm, second channel Vm. They bound the
+ * float32 rounding of the interpolated values (kink flags below). */
+static void corner_maxima(const or_vol *v, const double p[3], double *M, double *G, double *Hm, double *Vm) {
+    int i0[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) cell_of(p[a] / v->s[a] - 0.5, v->n[a], &i0[a], &f[a]);
+    *M = *G = *Hm = *Vm = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int64_t id = vidx(v->n, i0[0] + (c & 1), i0[1] + ((c >> 1) & 1), i0[2] + ((c >> 2) & 1));
+        const double *g = v->g + 3 * id, *H = v->H + 6 * id;
+        *M = fmax(*M, fabs(v->In[id]));
+        *G = fmax(*G, sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+        for (int q = 0; q < 6; ++q) *Hm = fmax(*Hm, fabs(H[q]));
+        if (v->V) *Vm = fmax(*Vm, fabs(v->V[id]));
+    }
+}
+
+/* Does the piecewise-linear table bend at knot jn along the intensity axis in row k,
+ * i.e. do the slopes on its two sides differ in some channel? Outside [0, w-1] the
+ * lookup is clamped (flat), so an end knot bends where the slope next to it is
+ * non-zero. Along the second axis likewise with the roles swapped (column j). */
+static int tf_bends_x(const double *tf, int w, int k, int jn) {
+    const double *r = tf + 4 * (size_t)k * w;
+    for (int c = 0; c < 4; ++c) {
+        double left = jn > 0 ? r[4 * jn + c] - r[4 * (jn - 1) + c] : 0.0;
+        double right = jn < w - 1 ? r[4 * (jn + 1) + c] - r[4 * jn + c] : 0.0;
+        if (left != right) return 1;
+    }
+    return 0;
+}
+
+static int tf_bends_y(const double *tf, int w, int h, int j, int kn) {
+    for (int c = 0; c < 4; ++c) {
+        double below = kn > 0 ? tf[4 * (kn * w + j) + c] - tf[4 * ((kn - 1) * w + j) + c] : 0.0;
+        double above = kn < h - 1 ? tf[4 * ((kn + 1) * w + j) + c] - tf[4 * (kn * w + j) + c] : 0.0;
+        if (below != above) return 1;
+    }
+    return 0;
+}
+
 /* Opacity (Eq. 4) and colour of one sample at world point p seen along unit dir.
  * kink (may be NULL) is set to 1 when the sample sits within float32 rounding of a
- * point where the opacity or colour is not differentiable in the voxels: a
- * transfer-function knot or end (lookup coordinate within 2e-4 entries), the clamps
- * of w(kappa) or of |grad I|/gmax or of alpha at 1 (within 1e-4), or a vanishing
- * gradient (|grad I| < 1e-4 gmax) where kappa and the shading normal are undefined.
- * There a float32 evaluation may take the other one-sided derivative. */
+ * point where the opacity or colour is not differentiable in the voxels: a knot or
+ * end of the transfer function where the table bends, the clamps of w(kappa), of
+ * |grad I|/gmax or of alpha at 1 (each window a worst-case float32 rounding bound
+ * of that quantity at this sample), or a vanishing gradient (|grad I| < 1e-4 gmax)
+ * where kappa and the shading normal are undefined. There a float32 evaluation may
+ * take the other one-sided derivative. */
 static void sample_optics_k(const or_vol *v, const or_params *P, const double *tf, const double p[3],
                             const double dir[3], double *alpha, double col[3], int *kink) {
     double fld[11];
@@ -306,13 +348,64 @@ static void sample_optics_k(const or_vol *v, const or_params *P, const double *t
     double w = clampd(winner, 0.0, P->w_max);
     double raw = P->opacity_scale * rgba[3] * mg * w;
     *alpha = clampd(raw, 0.0, 1.0);
-    if (kink) { /* exact zeros and ends are exact in float32 too: no flag there */
+    if (kink) {
+        /* Windows: how far float32 evaluation of the same sample can move each
+         * quantity, from worst-case rounding bounds (u = 2^-24 per IEEE operation;
+         * the interpolated values are sums of 8 products with rounded trilinear
+         * weights, the voxel-wise derivatives are rounded differences of the same
+         * float32 voxels, the sample position is good to 3e-8 voxel). A knot counts
+         * only where the table actually bends; exact zeros and ends (I = 0 or 1) are
+         * exact in float32 too and are not flagged. */
+        const double u = 5.9604644775390625e-8;
+        double M, G, Hm, Vm;
+        corner_maxima(v, p, &M, &G, &Hm, &Vm);
+        const double smin = fmin(v->s[0], fmin(v->s[1], v->s[2]));
+        const int w_ = P->tf_w, h_ = P->tf_h;
+        const double xs = clampd(fld[0], 0.0, 1.0) * (w_ - 1);
+        const double wx = (w_ - 1) * u * (12.0 * fabs(fld[0]) + M);
+        double ys = 0.0, wy = 0.0;
+        if (h_ > 1) {
+            ys = clampd(y, 0.0, 1.0) * (h_ - 1);
+            wy = P->tf_mode == 1 ? (h_ - 1) * (33.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn)
+                                 : (h_ - 1) * 10.0 * u * Vm;
+        }
+        const int jl = (int)fmin(floor(xs), w_ - 2), kl = h_ > 1 ? (int)fmin(floor(ys), h_ - 2) : 0;
         int k = 0;
-        if (fld[0] != 0.0 && fld[0] != 1.0) k |= frac_dist(clampd(fld[0], 0.0, 1.0) * (P->tf_w - 1)) < 2e-4;
-        if (P->tf_h > 1 && y != 0.0 && y != 1.0) k |= frac_dist(clampd(y, 0.0, 1.0) * (P->tf_h - 1)) < 2e-4;
-        if (P->gamma != 0.0 && gg > 0.0) k |= fabs(winner) < 1e-4 || fabs(winner - P->w_max) < 1e-4;
-        if (P->grad_mod) k |= fabs(gn - 1.0) < 1e-4;
-        k |= fabs(raw - 1.0) < 1e-4;
+        if (fld[0] != 0.0 && fld[0] != 1.0 && frac_dist(xs) < wx) {
+            const int jn = (int)floor(xs + 0.5);
+            k |= tf_bends_x(tf, w_, kl, jn) || (h_ > 1 && tf_bends_x(tf, w_, kl + 1, jn));
+        }
+        if (h_ > 1 && y != 0.0 && y != 1.0 && frac_dist(ys) < wy) {
+            const int kn = (int)floor(ys + 0.5);
+            k |= tf_bends_y(tf, w_, h_, jl, kn) || tf_bends_y(tf, w_, h_, jl + 1, kn);
+        }
+        /* |g|/gmax; kappa (its voxel Hessians are rounded second differences, and the
+         * gradient's rounding enters through dkappa/dg = 2 (H g - kappa g) / |g|^2) */
+        const double dgn = 33.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn;
+        double dwin = 0.0;
+        if (P->gamma != 0.0 && gg > 0.0) {
+            const double dk = 24.0 * u * M / (smin * smin) + 42.0 * u * Hm +
+                              50.0 * u * (3.0 * Hm + fabs(kappa)) * G / gmag + 8.0 * u * fabs(kappa);
+            dwin = fabs(P->gamma / P->kappa_ref) * dk + 2.0 * u;
+            k |= fabs(winner) < dwin || fabs(winner - P->w_max) < dwin;
+        }
+        if (P->grad_mod) k |= fabs(gn - 1.0) < dgn;
+        { /* alpha's clamp at 1: raw moves with the looked-up opacity and both factors */
+            const double *T = tf + 4 * (size_t)kl * w_;
+            double sx = fabs(T[4 * (jl + 1) + 3] - T[4 * jl + 3]), sy = 0.0;
+            if (h_ > 1) {
+                const double *T1 = T + 4 * (size_t)w_;
+                sx = fmax(sx, fabs(T1[4 * (jl + 1) + 3] - T1[4 * jl + 3]));
+                sy = fmax(fabs(T1[4 * jl + 3] - T[4 * jl + 3]), fabs(T1[4 * (jl + 1) + 3] - T[4 * (jl + 1) + 3]));
+            }
+            const double dca = sx * wx + sy * wy + 4.0 * u * fabs(rgba[3]);
+            const double dmg = P->grad_mod ? dgn : 0.0;
+            const double draw = P->opacity_scale * (dca * mg * w + fabs(rgba[3]) * (dmg * w + mg * dwin)) +
+                                4.0 * u * fabs(raw);
+            k |= fabs(raw - 1.0) < draw;
+        }
+        /* a vanishing gradient: kappa and the shading normal are undefined at g = 0 and
+         * ill-conditioned next to it (a conditioning guard, not a rounding bound) */
         if (P->shading || P->gamma != 0.0 || P->grad_mod || P->tf_mode == 1) k |= gn > 0.0 && gn < 1e-4;
         *kink = k;
     }

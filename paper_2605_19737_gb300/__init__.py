@@ -215,6 +215,12 @@ class Context:
         self._check(self._lib.vr_get_bricks(self._h, vol, grid.ctypes.data, empty.ctypes.data, nb))
         return grid, empty
 
+    def get_layout(self, vol):
+        """(bricks, intensity-brick store bytes, derived-brick store bytes) of a volume."""
+        nb, bb, db = ctypes.c_longlong(), ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        self._check(self._lib.vr_get_layout(self._h, vol, ctypes.byref(nb), ctypes.byref(bb), ctypes.byref(db)))
+        return nb.value, bb.value, db.value
+
     def get_normalized(self, vol):
         torch = _torch()
         nx, ny, nz = self._keep[vol]

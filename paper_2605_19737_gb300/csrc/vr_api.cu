@@ -658,6 +658,18 @@ vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigne
     return VR_OK;
 }
 
+vr_status vr_get_layout(vr_ctx* ctx, int vol_id, long long* nbricks, unsigned long long* brick_bytes,
+                        unsigned long long* derived_bytes) {
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "get_layout: unknown id %d", vol_id);
+    if (nbricks) *nbricks = v->nbricks;
+    if (brick_bytes) *brick_bytes = (unsigned long long)kBrickBytes * (unsigned long long)v->nbricks;
+    if (derived_bytes)
+        *derived_bytes = v->d_dbricks ? sizeof(float) * (unsigned long long)kDerBrickFloats * v->nbricks : 0ull;
+    return VR_OK;
+}
+
 vr_status vr_get_vesselness(vr_ctx* ctx, int vol_id, float* out, int out_on_device) {
     if (!ctx) return VR_ERR_INVALID_ARG;
     Volume* v = get_vol(ctx, vol_id);

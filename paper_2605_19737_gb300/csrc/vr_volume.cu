@@ -481,7 +481,40 @@ constexpr int kStaticMaxDevices = 64;
 static __device__ __align__(256) int g_static_prefix[kStaticTfMaxW + 1];
 
 std::mutex g_static_mu;
+// Per device: the device address of the static array and the id of the CUDA context
+// it was taken in. A device reset (cudaDeviceReset) destroys the context and the
+// module with it; the next call sees a new context id and looks the address up again.
 int* g_static_prefix_ptr[kStaticMaxDevices] = {};
+unsigned long long g_static_ctx_id[kStaticMaxDevices] = {};
+// Driver entry points for the current context and its process-unique id, resolved
+// through the runtime so that the library does not link the driver library itself.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_ctx_fns_resolved = false;
+
+// Id of the calling thread's current CUDA context, 0 when it cannot be told.
+unsigned long long current_ctx_id() {
+    if (!g_ctx_fns_resolved) {
+        g_ctx_fns_resolved = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        (void)cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    void* cu = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&cu) != 0 || !cu || g_ctx_get_id(cu, &id) != 0) return 0;
+    return id;
+}
 
 void put_msg(char* buf, int len, const char* msg) {
     if (!buf || len <= 0) return;
@@ -519,10 +552,13 @@ extern "C" vr_status vr_classify_bricks_noalloc(const unsigned short* d_grid, lo
     }
     int* prefix = nullptr;
     {
-        // once per device, with that device current: the device address of the
-        // static array (the host-side symbol is not a device pointer)
+        // once per device and CUDA context, with that device current: the device
+        // address of the static array (the host-side symbol is not a device pointer).
+        // A context id of 0 (no current context yet, or the driver cannot say) looks
+        // the address up on every call.
         std::lock_guard<std::mutex> lock(g_static_mu);
-        if (!g_static_prefix_ptr[dev]) {
+        unsigned long long id = current_ctx_id();
+        if (!g_static_prefix_ptr[dev] || id == 0 || id != g_static_ctx_id[dev]) {
             int* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_prefix);
             if (e != cudaSuccess || !p) {
@@ -530,7 +566,9 @@ extern "C" vr_status vr_classify_bricks_noalloc(const unsigned short* d_grid, lo
                 put_msg(h_msg, msg_len, "classify_bricks_noalloc: cudaGetSymbolAddress of the static scratch failed");
                 return VR_ERR_CUDA;
             }
+            if (id == 0) id = current_ctx_id();  // the lookup made the primary context current
             g_static_prefix_ptr[dev] = p;
+            g_static_ctx_id[dev] = id;
         }
         prefix = g_static_prefix_ptr[dev];
     }

@@ -254,6 +254,33 @@ def test_autograd_and_short_fit(vr, torch):
     vr.free_volume(vid)
 
 
+def test_data_parallel_fit_through_the_library(vr, torch):
+    """dp_fit with the library's per-shard step (one process: every view in one
+    shard) follows the plain autograd fit of the same MSE: same loss curve within
+    float32 summation-order differences, and the MSE falls."""
+    from paper_2605_19737_gb300 import autograd as ag
+    from paper_2605_19737_gb300 import fit as fitmod
+    from paper_2605_19737_gb300.distributed import dp_fit, library_shard_loss_grad
+    case = _cases()["head_1d"]
+    In32 = oracle.normalize(case["volume"]).astype(np.float32)
+    vid = _setup(vr, torch, case, In32)
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+    fixed = {k: v for k, v in case["params"].items() if k not in ag.PARAM_NAMES}
+    params = torch.tensor([case["params"][k] for k in ag.PARAM_NAMES], dtype=torch.float32)
+    rng = np.random.default_rng(76)
+    tf_target = np.clip(case["tf"] + rng.normal(0, 0.05, case["tf"].shape), 0, 1).astype(np.float32)
+    with torch.no_grad():
+        target = ag.render(vr, vid, torch.from_numpy(tf_target).cuda(), params, case["cams"], W, H, fixed)
+    tf0 = torch.from_numpy(case["tf"]).cuda()
+    f = library_shard_loss_grad(vr, vid, case["cams"], W, H, fixed, params, target)
+    x_dp, l_dp = dp_fit(f, tf0, n, steps=30, lr=1e-2)
+    x_ref, l_ref, _ = fitmod.fit_transfer_function(vr, vid, case["cams"], W, H, tf0, target, fixed, params, steps=30)
+    np.testing.assert_allclose(l_dp, l_ref, rtol=2e-3)
+    assert np.abs(x_dp.cpu().numpy() - x_ref.cpu().numpy()).max() < 2e-3
+    assert l_dp[-1] < 0.6 * l_dp[0], l_dp
+    vr.free_volume(vid)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("name", ["diff_head128_8cam", "brainweb_1080p"])
 def test_backward_full_size_sampled(vr, torch, name):
@@ -273,9 +300,9 @@ def test_backward_full_size_sampled(vr, torch, name):
     sampled = np.zeros((n, H, W), bool)
     sampled[:, ::16, ::16] = True
     amb = (fwd.flags & (oracle.FLAG_ET | oracle.FLAG_COUNT | oracle.FLAG_KINK)) != 0
-    # full-length rays (hundreds of samples) meet a knot or clamp within rounding more
-    # often than the small cases' rays: 7-8 % here
-    assert (amb & sampled).sum() <= 0.15 * sampled.sum()
+    # full-length rays (hundreds of samples) meet a knot or clamp within float32
+    # rounding more often than the small cases' rays: ~1 % here
+    assert (amb & sampled).sum() <= 0.05 * sampled.sum()
     dl = np.random.default_rng(75).normal(size=(n, H, W, 4)).astype(np.float32)
     dl[~sampled | amb] = 0.0
     dtf_o, dpar_o, dvol_o = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H,
