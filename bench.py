@@ -293,8 +293,15 @@ def run_batched(args, ctx, dev, flush):
             out = torch.empty((case["H"], case["W"], 4), device=dev)
             views.append((vid, case["cams"][c], out, case["W"], case["H"]))
     bid = ctx.batch_create(views)
-    tune = autotune.tune_batch(ctx, bid, "batched_4vol_64cam_512", reps=2, force=True,
-                               candidates=[(pw, w) for pw in (4, 8, 16) for w in (4, 8)])
+
+    def prepare(cells):  # skip-brick edge of every volume of the batch
+        for vid, case in zip(vids, cases):
+            ctx.set_brick_size(vid, cells)
+            ctx.precompute_morphology(vid)
+            ctx.set_tissue_params(vid, case["tf"], **case["params"])
+        ctx.batch_update(bid)
+    tune = autotune.tune_batch(ctx, bid, "batched_4vol_64cam_512", reps=2, force=True, prepare=prepare,
+                               candidates=[(4, 4), (4, 8), (8, 4), (16, 4)])
     pw, wpb = tune["packet_w"], tune["warps_per_block"]
     ctr = pkg.new_counters(dev.index)
     ctx.batch_render(bid, packet_w=pw, warps_per_block=wpb, counters=ctr)
@@ -329,9 +336,9 @@ def run_batched(args, ctx, dev, flush):
     return {"workload": "batched_4vol_64cam: 96^3, 128x160x128, 181x217x181, 256x256x176 float32; "
                         "64 orbit cameras each; 512x512", "views": len(views), "dense_samples": dense,
             "gsamples_per_s": dense / (batch_ms * 1e-3) / 1e9, "ms_per_batch": batch_ms,
-            "launch": "one persistent kernel from a CUDA graph", "autotuned": {"packet_w": pw,
-                                                                               "warps_per_block": wpb,
-                                                                               "timings_ms": tune["timings"]},
+            "launch": "one persistent kernel from a CUDA graph",
+            "autotuned": {"packet_w": pw, "warps_per_block": wpb, "brick": tune["brick"],
+                          "timings_ms": tune["timings"]},
             "single_view_gsamples_per_s": dense / (single_ms * 1e-3) / 1e9, "single_view_ms": single_ms}
 
 
@@ -377,9 +384,26 @@ def run(args):
 
     kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
               "stencil": pkg.VR_KERNEL_GATHER_STENCIL}[args.kernel]
+    # launch shape and skip-brick edge of the forward, tuned on this frame (the image
+    # does not depend on them)
+    shape = {"packet_w": 4, "warps_per_block": 4}
+    tuned = None
+    if args.kernel == "gather":
+        from paper_2605_19737_gb300 import autotune
+
+        def prepare(cells):
+            ctx.set_brick_size(vid, cells)
+            ctx.precompute_morphology(vid)
+            ctx.set_tissue_params(vid, case["tf"], **case["params"])
+        tuned = autotune.tune_render(ctx, vid, case["cams"], W, H, "brainweb_1080p", prepare=prepare, force=True,
+                                     out=out)
+        shape = {"packet_w": tuned["packet_w"], "warps_per_block": tuned["warps_per_block"]}
+        ctx.render(vid, case["cams"], W, H, out=out, counters=ctr.zero_(), **shape)
+        torch.cuda.synchronize()
+        rays, dense, evald, _, shaded, interp = [int(x) for x in ctr.cpu().numpy()[:6]]
 
     def frame():
-        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel)
+        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, **shape)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -431,7 +455,7 @@ def run(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ctx.set_tissue_params(vid, tf_host, **case["params"])
-        ctx.render(vid, case["cams"], W, H, out=img_host, kernel=kernel)
+        ctx.render(vid, case["cams"], W, H, out=img_host, kernel=kernel, **shape)
         ctx.synchronize()
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t1)
@@ -457,7 +481,7 @@ def run(args):
             flush.zero_()
             s0, s1, s2, s3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             s0.record()
-            ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, ray_state=state)
+            ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, ray_state=state, **shape)
             s1.record()
             ctx.render_backward(vid, case["cams"], W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol, ray_state=state)
             s2.record()
@@ -546,6 +570,8 @@ def run(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, ws), "kernel": args.kernel,
+            "tuned": None if tuned is None else {k: tuned[k] for k in ("packet_w", "warps_per_block", "brick",
+                                                                       "timings")},
             "fps": 1000.0 / ms, "fps_wall": fps_wall,
             "samples": {"dense_per_frame": dense, "evaluated_per_frame": evald, "interpolated_per_frame": interp,
                         "shaded_per_frame": shaded, "rays": rays},

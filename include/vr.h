@@ -125,7 +125,9 @@ typedef struct {
     int skip_empty;     /* 1: skip bricks classified empty (bit-neutral) */
     int packet_w;       /* rays per warp packet along x (packet = 32 rays): 4, 8 or 16 for the
                            per-lane kernels (default 4), also 32 for the staged and batched ones */
-    int warps_per_block;/* staged kernel: warps per CTA, 1..16 */
+    int warps_per_block;/* warps per CTA: the per-lane kernels 2, 4 (default) or 8 -- their CTA
+                           tile is min(warps, 16/packet_w) packets across and the rest down
+                           (4 warps: 16 x 8 pixels); the staged kernel 1..8 */
     void* ray_state;    /* NULL, or device memory of n_cams*H*W x 8 bytes (per-lane kernels
                            only): vr_render writes, per pixel, the index of the ray's last
                            sample (int32; -1 for none) and the transmittance in front of it
@@ -241,9 +243,20 @@ vr_status vr_set_normalized(vr_ctx* ctx, int vol_id, const float* d_norm);
  *   h_nb: 3 ints (nbx, nby, nbz). Any of them may be NULL. */
 vr_status vr_get_bricks(vr_ctx* ctx, int vol_id, unsigned short* h_grid, unsigned char* h_empty, int* h_nb);
 
+/* Edge of the skip bricks of a volume, in interpolation cells: 4, 8 (the default)
+ * or 16. The brick min/max grid, the empty-brick flags, the per-cell empty bits and
+ * the derived bricks of the voxel-wise derivatives are kept per skip brick; empty
+ * skip bricks are jumped a brick at a time. Rebuilds the grid at once; the volume
+ * then needs vr_precompute_morphology again (NOT_READY until then), which also
+ * re-classifies under the current tissue parameters. The images do not depend on
+ * the size (skipping is bit-neutral); the evaluated-sample counter does. The
+ * staged kernels (VR_KERNEL_STAGED) need 8. Synchronises.
+ * Errors: INVALID_ARG (unknown volume, other sizes), OOM, CUDA. */
+vr_status vr_set_brick_size(vr_ctx* ctx, int vol_id, int cells);
+
 /* Storage layout of a volume (no GPU work; any pointer may be NULL):
- *   nbricks:       bricks of 8^3 interpolation cells, nbx*nby*nbz;
- *   brick_bytes:   the intensity brick store (12^3 float32 per brick);
+ *   nbricks:       skip bricks (vr_set_brick_size), nbx*nby*nbz;
+ *   brick_bytes:   the intensity brick store (8^3-cell storage bricks, 12^3 float32 each);
  *   derived_bytes: the derived-brick store of the voxel-wise derivatives built by
  *                  vr_precompute_morphology (0 when it is not built).
  * Errors: INVALID_ARG (unknown volume). */

@@ -62,13 +62,13 @@ def _load():
         L.or_field_brute.argtypes = [_P, _P, _P, _P, _P]
         L.or_curvature.argtypes = [_P, _P, _P]
         L.or_tf_sample.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]
-        L.or_render.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.c_double, _P,
+        L.or_render.argtypes = [_P, _P, _P, _P, _P, ctypes.POINTER(Params), _P, _P, ctypes.c_int, ctypes.c_double, _P,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 _P, _P, _P, _P, _P, _P]
         L.or_render.restype = ctypes.c_int
         L.or_render_brute.argtypes = [_P, _P, _P, ctypes.POINTER(Params), _P, ctypes.c_double, _P,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]
-        L.or_brick_minmax_q.argtypes = [_P, _P, ctypes.c_float, ctypes.c_float, _P]
+        L.or_brick_minmax_q.argtypes = [_P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]
         L.or_classify.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int, ctypes.c_int, _P]
         L.or_gauss_smooth.argtypes = [_P, _P, ctypes.c_double, _P]
         L.or_eig3_jacobi.argtypes = [_P, _P]
@@ -200,8 +200,9 @@ class RenderResult:
 
 
 def render(In, spacing, params, tf, cams, W, H, V=None, brick_empty=None, gmax_value=0.0, pix_stride=1,
-           alternatives=True, v_amb=None):
-    """Render normalised volume ``In`` for cameras (n, 12) -> RenderResult with (n, H, W, 4) images."""
+           alternatives=True, v_amb=None, brick=8):
+    """Render normalised volume ``In`` for cameras (n, 12) -> RenderResult with (n, H, W, 4) images.
+    ``brick_empty``: flags of bricks of ``brick``^3 cells (the evaluated-sample counter)."""
     L = _load()
     In = _c(In, np.float64)
     Vc = None if V is None else _c(V, np.float64)
@@ -217,7 +218,7 @@ def render(In, spacing, params, tf, cams, W, H, V=None, brick_empty=None, gmax_v
     be = None if brick_empty is None else _c(brick_empty, np.uint8)
     va = None if v_amb is None else _c(v_amb, np.uint8)
     th = L.or_render(_ptr(In), _ptr(Vc), _ptr(va), _ptr(_dims(In)), _ptr(_c(spacing, np.float64)), ctypes.byref(params),
-                     _ptr(tf32), _ptr(be), float(gmax_value), _ptr(cams), n, W, H, pix_stride,
+                     _ptr(tf32), _ptr(be), int(brick), float(gmax_value), _ptr(cams), n, W, H, pix_stride,
                      _ptr(rgba), _ptr(lo), _ptr(hi), _ptr(dense), _ptr(ev), _ptr(fl))
     return RenderResult(rgba, lo, hi, dense, ev, fl, th)
 
@@ -266,15 +267,16 @@ def render_grad(In, spacing, params, tf, cams, W, H, dl_drgba, V=None, gmax_valu
 
 # ------------------------------------------------------- bricks and skipping
 
-def brick_minmax_q(raw):
-    """Quantised per-brick (qlo, qhi) of the normalised volume -> (nbz, nby, nbx, 2) uint16."""
+def brick_minmax_q(raw, brick=8):
+    """Quantised per-brick (qlo, qhi) of the normalised volume for bricks of
+    ``brick``^3 cells (4, 8 or 16) -> (nbz, nby, nbx, 2) uint16."""
     L = _load()
     r32 = _c(raw, np.float32)
     lo, hi = float(np.min(r32)), float(np.max(r32))
     nz, ny, nx = r32.shape
-    nb = [(n - 1 + 7) // 8 for n in (nx, ny, nz)]
+    nb = [(n - 1 + brick - 1) // brick for n in (nx, ny, nz)]
     grid = np.zeros((nb[2], nb[1], nb[0], 2), np.uint16)
-    L.or_brick_minmax_q(_ptr(r32), _ptr(_dims(r32)), lo, hi, _ptr(grid))
+    L.or_brick_minmax_q(_ptr(r32), _ptr(_dims(r32)), lo, hi, int(brick), _ptr(grid))
     return grid
 
 

@@ -63,6 +63,7 @@ typedef struct {
     const double *V;   /* vesselness or NULL */
     double gmax;
     const uint8_t *brick_empty; /* NULL or one byte per brick */
+    int bcells;                 /* cells per brick edge (4, 8 or 16) */
     int nb[3];
     const uint8_t *v_amb; /* NULL or 1 per voxel where V sits on an eigenvalue tie */
 } or_vol;
@@ -459,7 +460,7 @@ static int ray_setup(const or_vol *v, const double *cam, int W, int H, int i, in
     return *tn < *tf;
 }
 
-/* Brick of the cell that holds a sample: floor(i0 / 8) per axis. */
+/* Brick of the cell that holds a sample: floor(i0 / B) per axis, B = bcells. */
 static inline int64_t brick_of(const or_vol *v, const double p[3], int *near_face) {
     int b[3];
     *near_face = 0;
@@ -468,8 +469,8 @@ static inline int64_t brick_of(const or_vol *v, const double p[3], int *near_fac
         int i0;
         double f;
         cell_of(p[a] / v->s[a] - 0.5, v->n[a], &i0, &f);
-        b[a] = i0 / 8;
-        double m = floor(uc / 8.0 + 0.5) * 8.0; /* nearest multiple of 8 */
+        b[a] = i0 / v->bcells;
+        double m = floor(uc / v->bcells + 0.5) * v->bcells; /* nearest multiple of B */
         if (fabs(uc - m) < 1e-4 && m > 0.0 && m <= v->n[a] - 2) *near_face = 1;
     }
     return ((int64_t)b[2] * v->nb[1] + b[1]) * v->nb[0] + b[0];
@@ -533,6 +534,7 @@ static void march(const or_vol *v, const or_params *P, const double *tf, const d
 
 static void make_vol(or_vol *v, const double *In, const double *V, const int *n, const double *s) {
     memset(v, 0, sizeof *v);
+    v->bcells = 8;
     for (int a = 0; a < 3; ++a) {
         v->n[a] = n[a];
         v->s[a] = s[a];
@@ -546,19 +548,22 @@ static void make_vol(or_vol *v, const double *In, const double *V, const int *n,
  *   In: normalised volume; V: vesselness or NULL; v_amb: NULL or the tie mask of
  *   or_frangi (rays that interpolate V from a tie voxel get OR_FLAG_VAMB);
  *   gmax <= 0: computed here;
- *   brick_empty: NULL or the empty-brick flags (only the evaluated counter uses it);
+ *   brick_empty: NULL or the empty-brick flags of bricks of brick_cells^3 cells
+ *     (only the evaluated counter and the brick-face tie flag use them);
  *   rgba_lo / rgba_hi (nullable): the outcomes with et -/+ 1e-5 and with one
  *     sample less / more when the count is ambiguous -- every ray whose flags are
  *     non-zero has these alternatives filled, the rest are copies of rgba;
  *   pix_stride > 1 renders only pixels with i % stride == 0 and j % stride == 0.
  * Returns the number of OpenMP threads used. */
 int or_render(const double *In, const double *V, const uint8_t *v_amb, const int *n, const double *s,
-              const or_params *P, const float *tf32, const uint8_t *brick_empty, double gmax_in, const float *cams,
-              int n_cams,
+              const or_params *P, const float *tf32, const uint8_t *brick_empty, int brick_cells, double gmax_in,
+              const float *cams, int n_cams,
               int W, int H, int pix_stride, double *rgba, double *rgba_lo, double *rgba_hi, int64_t *dense,
               int64_t *evaluated, uint8_t *flags_out) {
     or_vol v;
     make_vol(&v, In, V, n, s);
+    v.bcells = brick_cells;
+    for (int a = 0; a < 3; ++a) v.nb[a] = (n[a] - 1 + brick_cells - 1) / brick_cells;
     int64_t nvox = (int64_t)n[0] * n[1] * n[2];
     double *g = (double *)malloc(sizeof(double) * 3 * nvox);
     double *Hs = (double *)malloc(sizeof(double) * 6 * nvox);
@@ -695,24 +700,24 @@ int or_render_brute(const double *In, const int *n, const double *s, const or_pa
 
 /* -------------------------------------- brick min/max grid and skipping */
 
-/* Per brick of 8^3 cells, the min and max of the normalised intensity over its
- * corner voxels [8b, min(8b+8, N-1)] per axis, quantised to 16 bits as
+/* Per brick of B^3 cells (B = 4, 8 or 16), the min and max of the normalised
+ * intensity over its corner voxels [Bb, min(Bb+B, N-1)] per axis, quantised to 16 bits as
  * qlo = floor(min * 65535), qhi = ceil(max * 65535). The normalisation and the
  * quantisation are taken in IEEE float32 with round-to-nearest, one operation at
  * a time (d = x - imin; r = d / (imax - imin); r * 65535), because these floats
  * decide integers that must match the kernel's bit for bit; codes are clamped to
  * [0, 65535]. raw holds float32 or uint16 values; grid is [nbz][nby][nbx][2]. */
-void or_brick_minmax_q(const float *raw, const int *n, float imin, float imax, uint16_t *grid) {
+void or_brick_minmax_q(const float *raw, const int *n, float imin, float imax, int B, uint16_t *grid) {
     int nb[3];
-    for (int a = 0; a < 3; ++a) nb[a] = (n[a] - 1 + 7) / 8;
+    for (int a = 0; a < 3; ++a) nb[a] = (n[a] - 1 + B - 1) / B;
     volatile float range = imax - imin;
     for (int bz = 0; bz < nb[2]; ++bz)
         for (int by = 0; by < nb[1]; ++by)
             for (int bx = 0; bx < nb[0]; ++bx) {
                 float lo = INFINITY, hi = -INFINITY;
-                for (int k = 8 * bz; k <= 8 * bz + 8 && k < n[2]; ++k)
-                    for (int j = 8 * by; j <= 8 * by + 8 && j < n[1]; ++j)
-                        for (int i = 8 * bx; i <= 8 * bx + 8 && i < n[0]; ++i) {
+                for (int k = B * bz; k <= B * bz + B && k < n[2]; ++k)
+                    for (int j = B * by; j <= B * by + B && j < n[1]; ++j)
+                        for (int i = B * bx; i <= B * bx + B && i < n[0]; ++i) {
                             volatile float d = raw[vidx(n, i, j, k)] - imin;
                             volatile float r = d / range;
                             if (r < lo) lo = r;

@@ -215,6 +215,10 @@ class Context:
         self._check(self._lib.vr_get_bricks(self._h, vol, grid.ctypes.data, empty.ctypes.data, nb))
         return grid, empty
 
+    def set_brick_size(self, vol, cells):
+        """Skip-brick edge in cells (4, 8 or 16); call precompute_morphology afterwards."""
+        self._check(self._lib.vr_set_brick_size(self._h, vol, int(cells)))
+
     def get_layout(self, vol):
         """(bricks, intensity-brick store bytes, derived-brick store bytes) of a volume."""
         nb, bb, db = ctypes.c_longlong(), ctypes.c_ulonglong(), ctypes.c_ulonglong()

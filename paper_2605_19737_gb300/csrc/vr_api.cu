@@ -25,9 +25,11 @@ namespace {
 
 struct Volume {
     int n[3] = {0, 0, 0};
-    int nb[3] = {0, 0, 0};
+    int nb[3] = {0, 0, 0};   // skip bricks per axis
+    int nsb[3] = {0, 0, 0};  // storage bricks (8^3 cells) per axis
+    int bs = 3;              // log2 of the cells per skip-brick edge
     float s[3] = {1, 1, 1};
-    long long nvox = 0, nbricks = 0;
+    long long nvox = 0, nbricks = 0, nsbricks = 0;  // voxels, skip bricks, storage bricks
     float* d_norm = nullptr;
     float* d_bricks = nullptr;
     uint16_t* d_grid = nullptr;
@@ -57,6 +59,7 @@ struct Batch {
     int* d_prefix = nullptr;        // 4 packet shapes x n_views
     int n_work[4] = {0, 0, 0, 0};   // packets per packet shape (packet_w = 4, 8, 16, 32)
     bool all_derived = false;       // every view's volume has derived bricks
+    int bs = 3;                     // the skip-brick size all views share, 0 when they differ
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (packet_w, warps) -> graph
 };
 
@@ -226,8 +229,11 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
     for (int a = 0; a < 3; ++a) {
         L.vol.n[a] = v->n[a];
         L.vol.nb[a] = v->nb[a];
+        L.vol.nsb[a] = v->nsb[a];
         L.vol.s[a] = v->s[a];
     }
+    L.vol.bs = v->bs;
+    L.vol.der_stride = (int)der_brick_floats(v->bs);
     L.vol.bricks = v->d_bricks;
     L.vol.vbricks = (v->tp.tf_mode == 2) ? v->d_vbricks : nullptr;
     L.vol.dbricks = v->d_dbricks;
@@ -242,10 +248,11 @@ void fill_launch(RenderLaunch& L, const Volume* v, int W, int H, int skip) {
 }
 
 vr_status rebuild_bricks(vr_ctx* ctx, Volume* v) {
-    CK(launch_make_bricks(v->d_norm, v->n, v->nb, v->d_bricks, ctx->stream), "bricking");
-    CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->d_grid, ctx->stream), "brick min/max");
-    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
-    if (v->d_cellq) CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
+    CK(launch_make_bricks(v->d_norm, v->n, v->nsb, v->d_bricks, ctx->stream), "bricking");
+    CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->bs, v->d_grid, ctx->stream), "brick min/max");
+    if (v->d_dbricks)
+        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->bs, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    if (v->d_cellq) CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->bs, v->d_cellq, ctx->stream), "cell min/max");
     return VR_OK;
 }
 
@@ -255,7 +262,7 @@ vr_status classify_volume(vr_ctx* ctx, Volume* v) {
     CK(launch_classify(v->d_grid, v->nbricks, v->d_tf, v->tp.tf_w, v->tp.tf_h, v->d_empty, v->d_prefix, ctx->stream),
        "classify");
     if (v->d_cellmask)
-        CK(launch_classify_cells(v->d_cellq, v->nbricks, v->d_prefix, v->tp.tf_w, v->d_cellmask, ctx->stream),
+        CK(launch_classify_cells(v->d_cellq, v->nbricks, v->bs, v->d_prefix, v->tp.tf_w, v->d_cellmask, ctx->stream),
            "classify cells");
     return VR_OK;
 }
@@ -380,13 +387,17 @@ vr_status vr_load_volume(vr_ctx* ctx, const void* data, int on_device, vr_dtype 
     Volume* v = new Volume();
     v->n[0] = nx, v->n[1] = ny, v->n[2] = nz;
     v->s[0] = sx, v->s[1] = sy, v->s[2] = sz;
-    for (int a = 0; a < 3; ++a) v->nb[a] = (v->n[a] - 1 + kCells - 1) / kCells;
+    for (int a = 0; a < 3; ++a) {
+        v->nb[a] = (v->n[a] - 1 + (1 << v->bs) - 1) >> v->bs;
+        v->nsb[a] = (v->n[a] - 1 + kCells - 1) / kCells;
+    }
     v->nvox = (long long)nx * ny * nz;
     v->nbricks = (long long)v->nb[0] * v->nb[1] * v->nb[2];
+    v->nsbricks = (long long)v->nsb[0] * v->nsb[1] * v->nsb[2];
     const size_t esz = dtype == VR_F32 ? 4 : 2;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dalloc(ctx, &v->d_norm, sizeof(float) * v->nvox);
-    if (e == cudaSuccess) e = dalloc(ctx, &v->d_bricks, (size_t)kBrickBytes * v->nbricks);
+    if (e == cudaSuccess) e = dalloc(ctx, &v->d_bricks, (size_t)kBrickBytes * v->nsbricks);
     if (e == cudaSuccess) e = dalloc(ctx, &v->d_grid, sizeof(uint16_t) * 2 * v->nbricks);
     if (e == cudaSuccess) e = dalloc(ctx, &v->d_empty, v->nbricks);
     if (e == cudaSuccess) e = dalloc(ctx, &v->d_vc, sizeof(VolConst));
@@ -452,7 +463,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     v->morph_ready = false;  // until every step below has been issued
     CK(launch_gmax(v->d_norm, v->n, v->s, v->d_vc, ctx->stream), "gmax");
     // voxel-wise derivatives for the raymarch (Sec. 2.3), within a memory budget
-    const size_t dbytes = sizeof(float) * (size_t)kDerBrickFloats * v->nbricks;
+    const size_t dbytes = sizeof(float) * (size_t)der_brick_floats(v->bs) * v->nbricks;
     if (v->d_dbricks && dbytes > ctx->derived_budget) {
         CK(cudaStreamSynchronize(ctx->stream), "precompute_morphology: sync");
         dfree(ctx, v->d_dbricks);
@@ -467,11 +478,12 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
     }
     // per-cell min/max (4 B per cell) and per-cell empty bits, for either path
     if (!v->d_cellq)
-        CK(dalloc(ctx, &v->d_cellq, sizeof(uint16_t) * 2 * kCellsPerBrick * (size_t)v->nbricks), "cell grid");
+        CK(dalloc(ctx, &v->d_cellq, (sizeof(uint16_t) * 2 * (size_t)v->nbricks) << (3 * v->bs)), "cell grid");
     if (!v->d_cellmask)
-        CK(dalloc(ctx, &v->d_cellmask, sizeof(uint32_t) * (kCellsPerBrick / 32) * (size_t)v->nbricks), "cell flags");
-    if (v->d_dbricks) CK(launch_make_derived(v->d_norm, v->n, v->nb, v->s, v->d_dbricks, ctx->stream), "derived bricks");
-    CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->d_cellq, ctx->stream), "cell min/max");
+        CK(dalloc(ctx, &v->d_cellmask, sizeof(uint32_t) * (size_t)cell_words(v->bs) * v->nbricks), "cell flags");
+    if (v->d_dbricks)
+        CK(launch_make_derived(v->d_norm, v->n, v->nb, v->bs, v->s, v->d_dbricks, ctx->stream), "derived bricks");
+    CK(launch_cell_minmax(v->d_norm, v->n, v->nb, v->bs, v->d_cellq, ctx->stream), "cell min/max");
     if (v->params_ready) {
         vr_status cs = classify_volume(ctx, v);
         if (cs != VR_OK) return cs;
@@ -480,7 +492,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         v->v_ready = false;
         if (v->params_ready && v->tp.tf_mode == 2) v->params_ready = false;  // its V channel is being replaced
         if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "vesselness volume");
-        if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "vesselness bricks");
+        if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nsbricks), "vesselness bricks");
         if (!v->d_smax) CK(dalloc(ctx, &v->d_smax, sizeof(float) * 8), "vesselness scale maxima");
         const size_t need = sizeof(float) * 2 * (size_t)v->nvox;  // smoothed volume + smoothing pass
         if (ctx->scratch_cap < need) {
@@ -494,7 +506,7 @@ vr_status vr_precompute_morphology(vr_ctx* ctx, int vol_id, const float* h_sigma
         CK(launch_frangi(v->d_norm, v->n, h_sigmas, n_sigmas, ctx->d_scratch, ctx->d_scratch + v->nvox, v->d_smax,
                          v->d_vessel, ctx->stream),
            "vesselness");
-        CK(launch_make_bricks(v->d_vessel, v->n, v->nb, v->d_vbricks, ctx->stream), "vesselness bricks");
+        CK(launch_make_bricks(v->d_vessel, v->n, v->nsb, v->d_vbricks, ctx->stream), "vesselness bricks");
         v->v_ready = true;
     }
     v->morph_ready = true;
@@ -620,7 +632,7 @@ vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int 
     v->v_ready = false;
     if (v->params_ready && v->tp.tf_mode == 2) v->params_ready = false;
     if (!v->d_vessel) CK(dalloc(ctx, &v->d_vessel, sizeof(float) * v->nvox), "load_second_channel: channel volume");
-    if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nbricks), "load_second_channel: bricks");
+    if (!v->d_vbricks) CK(dalloc(ctx, &v->d_vbricks, (size_t)kBrickBytes * v->nsbricks), "load_second_channel: bricks");
     if (!v->d_ch2) CK(dalloc(ctx, &v->d_ch2, sizeof(float) * 8), "load_second_channel: normalisation constants");
     const size_t esz = dtype == VR_F32 ? 4 : 2;
     const void* raw = data;
@@ -631,7 +643,7 @@ vr_status vr_load_second_channel(vr_ctx* ctx, int vol_id, const void* data, int 
     CK(launch_normalize(raw, dtype, v->nvox, v->d_ch2, reinterpret_cast<VolConst*>(v->d_ch2 + 4), v->d_vessel,
                         ctx->stream),
        "load_second_channel: normalise");
-    CK(launch_make_bricks(v->d_vessel, v->n, v->nb, v->d_vbricks, ctx->stream), "load_second_channel: bricking");
+    CK(launch_make_bricks(v->d_vessel, v->n, v->nsb, v->d_vbricks, ctx->stream), "load_second_channel: bricking");
     float mm[2] = {0, 0};
     CK(cudaMemcpyAsync(mm, v->d_ch2, sizeof mm, cudaMemcpyDeviceToHost, ctx->stream), "load_second_channel: read back");
     CK(cudaStreamSynchronize(ctx->stream), "load_second_channel: sync");
@@ -664,9 +676,40 @@ vr_status vr_get_layout(vr_ctx* ctx, int vol_id, long long* nbricks, unsigned lo
     Volume* v = get_vol(ctx, vol_id);
     if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "get_layout: unknown id %d", vol_id);
     if (nbricks) *nbricks = v->nbricks;
-    if (brick_bytes) *brick_bytes = (unsigned long long)kBrickBytes * (unsigned long long)v->nbricks;
+    if (brick_bytes) *brick_bytes = (unsigned long long)kBrickBytes * (unsigned long long)v->nsbricks;
     if (derived_bytes)
-        *derived_bytes = v->d_dbricks ? sizeof(float) * (unsigned long long)kDerBrickFloats * v->nbricks : 0ull;
+        *derived_bytes = v->d_dbricks ? sizeof(float) * (unsigned long long)der_brick_floats(v->bs) * v->nbricks : 0ull;
+    return VR_OK;
+}
+
+vr_status vr_set_brick_size(vr_ctx* ctx, int vol_id, int cells) {
+    NvtxRange range_("vr_set_brick_size");
+    if (!ctx) return VR_ERR_INVALID_ARG;
+    Volume* v = get_vol(ctx, vol_id);
+    if (!v) return fail(ctx, VR_ERR_INVALID_ARG, "set_brick_size: unknown id %d", vol_id);
+    int bs = -1;
+    for (int q = kMinBrickShift; q <= kMaxBrickShift; ++q)
+        if (cells == (1 << q)) bs = q;
+    if (bs < 0) return fail(ctx, VR_ERR_INVALID_ARG, "set_brick_size: %d cells per brick edge; 4, 8 or 16", cells);
+    if (bs == v->bs) return VR_OK;
+    DeviceGuard g(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream), "set_brick_size sync");
+    // the grid, flags, cells and derived bricks follow the new size; the derived
+    // bricks and the cell grid are rebuilt by the next vr_precompute_morphology
+    v->morph_ready = false;
+    dfree(ctx, v->d_grid);
+    dfree(ctx, v->d_empty);
+    dfree(ctx, v->d_dbricks);
+    dfree(ctx, v->d_cellq);
+    dfree(ctx, v->d_cellmask);
+    v->d_grid = nullptr, v->d_empty = nullptr, v->d_dbricks = nullptr, v->d_cellq = nullptr, v->d_cellmask = nullptr;
+    v->bs = bs;
+    for (int a = 0; a < 3; ++a) v->nb[a] = (v->n[a] - 1 + (1 << bs) - 1) >> bs;
+    v->nbricks = (long long)v->nb[0] * v->nb[1] * v->nb[2];
+    CK(dalloc(ctx, &v->d_grid, sizeof(uint16_t) * 2 * v->nbricks), "set_brick_size: grid");
+    CK(dalloc(ctx, &v->d_empty, v->nbricks), "set_brick_size: flags");
+    CK(cudaMemsetAsync(v->d_empty, 0, v->nbricks, ctx->stream), "set_brick_size: flags");
+    CK(launch_brick_minmax(v->d_norm, v->n, v->nb, v->bs, v->d_grid, ctx->stream), "set_brick_size: brick min/max");
     return VR_OK;
 }
 
@@ -769,10 +812,14 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     const bool staged = o.kernel == VR_KERNEL_STAGED;
     if (staged && (o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16 && o.packet_w != 32))
         return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8, 16 or 32");
+    if (staged && v->bs != 3)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: the staged kernel stages 8^3-cell bricks (vr_set_brick_size 8)");
     if (staged && (o.warps_per_block < 1 || o.warps_per_block > 8))
         return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be in [1, 8]");
     if (!staged && o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16)
         return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8 or 16 for the per-lane kernels");
+    if (!staged && o.warps_per_block != 2 && o.warps_per_block != 4 && o.warps_per_block != 8)
+        return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be 2, 4 or 8 for the per-lane kernels");
     DeviceGuard g(ctx->device);
     float* dst = out_rgba;
     const size_t img_bytes = sizeof(float) * 4 * (size_t)n_cams * W * H;
@@ -814,7 +861,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
             CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), ctx->stream), "render: reset work counter");
             CK(launch_render_staged(L, o.warps_per_block, ctas < need ? ctas : need, ctx->stream), "render kernel");
         } else {
-            CK(launch_render_gather(L, ctx->stream), "render kernel");
+            CK(launch_render_gather(L, o.warps_per_block, ctx->stream), "render kernel");
         }
     }
     if (out_on_host)
@@ -849,6 +896,9 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (staged || (opts && opts->kernel == VR_KERNEL_GATHER_STENCIL)) B.r.vol.dbricks = nullptr;
     B.r.packet_w = opts ? opts->packet_w : 4;
     B.r.ray_state = opts ? static_cast<float2*>(opts->ray_state) : nullptr;
+    if (staged && v->bs != 3)
+        return fail(ctx, VR_ERR_INVALID_ARG,
+                    "render_backward: the staged kernel stages 8^3-cell bricks (vr_set_brick_size 8)");
     if (staged && B.r.ray_state)
         return fail(ctx, VR_ERR_INVALID_ARG, "render_backward: ray_state needs a per-lane kernel");
     if (!staged && B.r.packet_w != 4 && B.r.packet_w != 8 && B.r.packet_w != 16)
@@ -932,6 +982,7 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
         b->n_work[si] = acc;
     }
     bool all_derived = true;
+    int bs = -1;
     for (int i = 0; i < n; ++i) {
         const vr_view& vw = b->views[i];
         Volume* v = get_vol(ctx, vw.vol_id);
@@ -950,13 +1001,15 @@ vr_status batch_upload(vr_ctx* ctx, Batch* b) {
         d.H = vw.H;
         d.rc = L.rc;
         all_derived = all_derived && L.vol.dbricks != nullptr;
+        bs = (bs < 0 || bs == v->bs) ? v->bs : 0;
     }
-    if (all_derived != b->all_derived) {
-        // the captured graphs launch the other kernel variant
+    if (all_derived != b->all_derived || bs != b->bs) {
+        // the captured graphs launch another kernel variant
         if (ctx->graph_stream) CK(cudaStreamSynchronize(ctx->graph_stream), "batch: graph sync");
         for (auto& gx : b->graphs) cudaGraphExecDestroy(gx.second);
         b->graphs.clear();
         b->all_derived = all_derived;
+        b->bs = bs;
     }
     CK(cudaMemcpyAsync(b->d_views, b->table.data(), sizeof(ViewDev) * n, cudaMemcpyHostToDevice, ctx->stream),
        "batch: upload views");
@@ -990,7 +1043,7 @@ vr_status batch_enqueue(vr_ctx* ctx, Batch* b, const vr_render_opts& o, vr_count
     if (ctas > need) ctas = need;
     if (ctas < 1) ctas = 1;
     CK(cudaMemsetAsync(ctx->d_work + 2, 0, sizeof(unsigned), st), "batch: reset work counter");
-    CK(launch_render_batch(B, o.warps_per_block, ctas, b->all_derived, st), "batch kernel");
+    CK(launch_render_batch(B, o.warps_per_block, ctas, b->all_derived, b->bs, st), "batch kernel");
     return VR_OK;
 }
 

@@ -44,18 +44,22 @@ __device__ __forceinline__ long long bidx(const VolumeDev& v, const int b[3]) {
 // the Hessian channels are read even without a curvature term (gamma = 0): the
 // forward values do not need them then, but dL/dgamma = sum dL/dw kappa / kappa_ref
 // does.
-template <bool kDerived, bool kHessian>
-__device__ __forceinline__ void eval_field(const VolumeDev& v, const TissueDev& tp, long long bi, const int i0[3], const int bc[3], int base,
-                                           const float f[3], const float is[3], float fld[10]) {
+// bi: the skip brick of the sample's cell (derived bricks); sbi, base: its storage
+// brick and the stencil origin in it (intensity bricks).
+template <bool kDerived, bool kHessian, int kBS>
+__device__ __forceinline__ void eval_field(const VolumeDev& v, const TissueDev& tp, long long bi, long long sbi,
+                                           const int i0[3], int base, const float f[3], const float is[3],
+                                           float fld[10]) {
     if (kDerived) {
-        const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats);
-        derived_channels<true, 0, 4>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld);
+        const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * der_brick_floats(kBS));
+        const int m = (1 << kBS) - 1, E = m + 2;
+        derived_channels<true, 0, 4>(brick, E, i0[0] & m, i0[1] & m, i0[2] & m, f[0], f[1], f[2], fld);
         if (kHessian)
-            derived_channels<true, 4, 6>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld + 4);
+            derived_channels<true, 4, 6>(brick, E, i0[0] & m, i0[1] & m, i0[2] & m, f[0], f[1], f[2], fld + 4);
         else
-            load_hessian<true>(tp, brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f, fld);
+            load_hessian<true>(tp, brick, E, i0[0] & m, i0[1] & m, i0[2] & m, f, fld);
     } else {
-        field_eval(GLoad{v.bricks + bi * kBrickVox}, base, f[0], f[1], f[2], fld);
+        field_eval(GLoad{v.bricks + sbi * kBrickVox}, base, f[0], f[1], f[2], fld);
         scale_field(fld, is);
     }
 }
@@ -168,7 +172,8 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
 // Derived bricks without a curvature term (gamma = 0): with kLazyHessian a sample
 // reads the Hessian only when its opacity entry is non-zero (for dL/dgamma); with
 // kNoHessian, when no uniform gradient is wanted, never.
-template <bool kDerived, bool kLazyHessian, bool kNoHessian = false>
+// kBS: log2 of the skip-brick edge (2, 3, 4), fixed at compile time.
+template <bool kDerived, bool kLazyHessian, bool kNoHessian, int kBS>
 __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     const RenderLaunch& L = B.r;
     const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
     TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ntf, L.tp.tf_w, L.tp.tf_h > 1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
-    tile_pixel(L.packet_w, w, l, di, dj);
+    tile_pixel(L.packet_w, __ffs(tile_packets_x(L.packet_w, 4)) - 1, w, l, di, dj);
     const int i = blockIdx.x * 16 + di;
     const int j = blockIdx.y * 8 + dj;
     const int cam = blockIdx.z;
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
-                    bc[q] = i0[q] >> 3;
+                    bc[q] = i0[q] >> kBS;
                 }
                 if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
                                                (unsigned)i0[1] <= (unsigned)(v.n[1] - 2) &&
@@ -226,15 +231,15 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                     break;
                 const long long bi = bidx(v, bc);
                 if (L.skip && __ldg(v.empty + bi)) {
-                    k = brick_exit_k(r, bc, k, r.ns);
+                    k = brick_exit_k(r, bc, 1 << kBS, k, r.ns);
                     continue;
                 }
-                const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
-                                 (i0[0] - kCells * bc[0]);
+                int base;
+                const long long sbi = storage_brick(v, i0, base);
                 float fld[10];
-                eval_field<kDerived, false>(v, L.tp, bi, i0, bc, base, f, is, fld);
+                eval_field<kDerived, false, kBS>(v, L.tp, bi, sbi, i0, base, f, is, fld);
                 const float vval =
-                    v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+                    v.vbricks ? value_eval(GLoad{v.vbricks + sbi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 float alpha, col[3];
                 sample_optics(fld, vval, r.dir, L.tp, tf, inv_gmax, alpha, col);
                 const float wgt = (1.0f - A) * alpha;  // as the forward kernel composites
@@ -266,7 +271,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
-                    bc[q] = i0[q] >> 3;
+                    bc[q] = i0[q] >> kBS;
                 }
                 // No skipping here: a sample in an empty brick has alpha = 0, but its lookup
                 // still gives the opacity entries it reads a non-zero gradient.
@@ -275,21 +280,22 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                                                (unsigned)i0[2] <= (unsigned)(v.n[2] - 2)))
                     continue;
                 const long long bi = bidx(v, bc);
-                const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
-                                 (i0[0] - kCells * bc[0]);
+                int base;
+                const long long sbi = storage_brick(v, i0, base);
                 float fld[10];
                 const float vval =
-                    v.vbricks ? value_eval(GLoad{v.vbricks + bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
+                    v.vbricks ? value_eval(GLoad{v.vbricks + sbi * kBrickVox}, base, f[0], f[1], f[2]) : 0.f;
                 SampleOptics so;
                 if (kLazyHessian) {
                     // I and the gradient, the table lookup, then the Hessian, which without
                     // a curvature term only dL/dgamma needs -- and not at a zero opacity
                     // entry (dL/dw = 0 there, and w = 1 whatever kappa)
-                    const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * kDerBrickFloats);
-                    derived_channels<true, 0, 4>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2], fld);
+                    const float4* brick = reinterpret_cast<const float4*>(v.dbricks + bi * der_brick_floats(kBS));
+                    const int m = (1 << kBS) - 1, E = m + 2;
+                    derived_channels<true, 0, 4>(brick, E, i0[0] & m, i0[1] & m, i0[2] & m, f[0], f[1], f[2], fld);
                     optics_tf(fld, vval, L.tp, tf, inv_gmax, so);
                     if (!kNoHessian && so.c.w != 0.0f) {
-                        derived_channels<true, 4, 6>(brick, i0[0] & 7, i0[1] & 7, i0[2] & 7, f[0], f[1], f[2],
+                        derived_channels<true, 4, 6>(brick, E, i0[0] & m, i0[1] & m, i0[2] & m, f[0], f[1], f[2],
                                                      fld + 4);
                     } else {
 #pragma unroll
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                     }
                     optics_rest(fld, r.dir, L.tp, so);
                 } else {
-                    eval_field<kDerived, true>(v, L.tp, bi, i0, bc, base, f, is, fld);
+                    eval_field<kDerived, true, kBS>(v, L.tp, bi, sbi, i0, base, f, is, fld);
                     optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
                 }
                 const float alpha = so.alpha, col[3] = {so.col[0], so.col[1], so.col[2]};
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
                 break;
             const long long bi = bidx(v, bc);
             if (L.skip && __ldg(v.empty + bi)) {
-                k = brick_exit_k(r, bc, k, r.ns);
+                k = brick_exit_k(r, bc, kCells, k, r.ns);
                 continue;
             }
             const int base = ((i0[2] - kCells * bc[2]) * kEdge + (i0[1] - kCells * bc[1])) * kEdge +
@@ -602,6 +608,20 @@ cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, fl
     return cudaGetLastError();
 }
 
+template <int kBS>
+void launch_backward_bs(const BackwardLaunch& B, dim3 grid, cudaStream_t st) {
+    const RenderLaunch& L = B.r;
+    if (L.vol.dbricks)
+        if (L.tp.gk == 0.0f && !B.dparams)
+            k_render_backward<true, true, true, kBS><<<grid, 128, 0, st>>>(B);
+        else if (L.tp.gk == 0.0f)
+            k_render_backward<true, true, false, kBS><<<grid, 128, 0, st>>>(B);
+        else
+            k_render_backward<true, false, false, kBS><<<grid, 128, 0, st>>>(B);
+    else
+        k_render_backward<false, false, false, kBS><<<grid, 128, 0, st>>>(B);
+}
+
 cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st) {
     const RenderLaunch& L = B.r;
     dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
@@ -613,15 +633,11 @@ cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStr
         k_render_backward_staged<<<grid, 128, smem, st>>>(B);
         return cudaGetLastError();
     }
-    if (L.vol.dbricks)
-        if (L.tp.gk == 0.0f && !B.dparams)
-            k_render_backward<true, true, true><<<grid, 128, 0, st>>>(B);
-        else if (L.tp.gk == 0.0f)
-            k_render_backward<true, true><<<grid, 128, 0, st>>>(B);
-        else
-            k_render_backward<true, false><<<grid, 128, 0, st>>>(B);
-    else
-        k_render_backward<false, false><<<grid, 128, 0, st>>>(B);
+    switch (L.vol.bs) {
+        case 2: launch_backward_bs<2>(B, grid, st); break;
+        case 4: launch_backward_bs<4>(B, grid, st); break;
+        default: launch_backward_bs<3>(B, grid, st); break;
+    }
     return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ namespace {
 // volume has derived bricks, so only that path is compiled in and the kernel is
 // held to 72 registers (measured: 110 Gsamples/s on the 256-view batch, against
 // 102 at 64 registers); otherwise each view takes its own path at run time.
-template <bool kAllDerived>
+template <bool kAllDerived, int kBS>
 __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
     const int lane = threadIdx.x & 31;
     unsigned rays_hit = 0, dense_tot = 0, eval_tot = 0, shade_tot = 0, interp_tot = 0;
@@ -45,11 +45,11 @@ __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
         unsigned dense = 0, evald = 0, shaded = 0, interp = 0;
         if (hit) {
             if (kAllDerived || v.dbricks)
-                march_gather<true, false, false, false>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
-                                   dense, evald, shaded, interp);
+                march_gather<true, false, false, false, kBS>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r,
+                                                             B.skip, inv_gmax, is, out, dense, evald, shaded, interp);
             else
-                march_gather<false>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r, B.skip, inv_gmax, is, out,
-                                    dense, evald, shaded, interp);
+                march_gather<false, false, false, true, kBS>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r,
+                                                             B.skip, inv_gmax, is, out, dense, evald, shaded, interp);
         }
         if (inside) reinterpret_cast<float4*>(vw.out)[(long long)j * vw.W + i] = out;
         rays_hit += hit ? 1u : 0u;
@@ -61,26 +61,42 @@ __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
     if (B.counters) add_counters(B.counters, rays_hit, dense_tot, eval_tot, 0u, shade_tot, interp_tot);
 }
 
-__global__ void __maxnreg__(72) k_render_batch_derived(const __grid_constant__ BatchLaunch B) { batch_body<true>(B); }
+// kBS: the skip-brick size shared by every view, or 0 when the views mix sizes.
+template <int kBS>
+__global__ void __maxnreg__(72) k_render_batch_derived(const __grid_constant__ BatchLaunch B) {
+    batch_body<true, kBS>(B);
+}
 
 __global__ void __launch_bounds__(256, 3) k_render_batch_mixed(const __grid_constant__ BatchLaunch B) {
-    batch_body<false>(B);
+    batch_body<false, 0>(B);
+}
+
+template <int kBS>
+cudaError_t derived_ctas(int threads, int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_derived<kBS>, threads, 0);
 }
 
 }  // namespace
 
 cudaError_t batch_ctas_per_sm(int warps_per_block, bool all_derived, int* per_sm) {
-    return all_derived
-               ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_derived, warps_per_block * 32, 0)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_mixed, warps_per_block * 32, 0);
+    return all_derived ? derived_ctas<3>(warps_per_block * 32, per_sm)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_render_batch_mixed,
+                                                                       warps_per_block * 32, 0);
 }
 
-cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived, int bs,
                                 cudaStream_t st) {
-    if (all_derived)
-        k_render_batch_derived<<<ctas, warps_per_block * 32, 0, st>>>(B);
+    const int t = warps_per_block * 32;
+    if (!all_derived)
+        k_render_batch_mixed<<<ctas, t, 0, st>>>(B);
+    else if (bs == 2)
+        k_render_batch_derived<2><<<ctas, t, 0, st>>>(B);
+    else if (bs == 3)
+        k_render_batch_derived<3><<<ctas, t, 0, st>>>(B);
+    else if (bs == 4)
+        k_render_batch_derived<4><<<ctas, t, 0, st>>>(B);
     else
-        k_render_batch_mixed<<<ctas, warps_per_block * 32, 0, st>>>(B);
+        k_render_batch_derived<0><<<ctas, t, 0, st>>>(B);
     return cudaGetLastError();
 }
 

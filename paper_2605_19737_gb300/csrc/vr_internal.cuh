@@ -1,12 +1,16 @@
 // vr_internal.cuh -- declarations shared by the library's translation units.
 //
-// Volume storage: the volume is cut into bricks of 8^3 interpolation cells
-// (cell i0 spans voxels i0 and i0+1 along each axis; a sample whose clamped
-// coordinate u_c has floor cell i0 = min(floor(u_c), N-2) belongs to brick
-// i0 / 8). Each brick is stored as a dense 12^3 float32 block holding voxels
-// [8b-1, 8b+11) per axis with clamp-to-edge values outside the volume: the
-// 4-tap stencils of a cell (voxels i0-1 .. i0+2) always fall inside it. The
-// block is 6912 bytes (a multiple of 16), so one bulk copy moves it.
+// Volume storage. Interpolation cell i0 spans voxels i0 and i0+1 along each axis;
+// a sample whose clamped coordinate u_c has floor cell i0 = min(floor(u_c), N-2)
+// lies in that cell. Two brick grids cut the cells:
+//  * storage bricks of 8^3 cells hold the intensities (and the second channel)
+//    for the per-sample stencils: a dense 12^3 float32 block of voxels
+//    [8b-1, 8b+11) per axis with clamp-to-edge values outside the volume, so the
+//    4-tap stencils of a cell (voxels i0-1 .. i0+2) fall inside it; 6912 bytes
+//    (a multiple of 16), one bulk copy moves it;
+//  * skip bricks of B^3 cells (B = 2^bs, 4, 8 or 16; 8 by default) carry the
+//    quantised min/max grid, the empty flags, the per-cell empty bits and the
+//    derived bricks of the voxel-wise derivatives, (B+1)^3 corners each.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,12 +28,20 @@ constexpr int kBrickVox = kEdge * kEdge * kEdge;   // 1728 floats
 constexpr int kBrickBytes = kBrickVox * 4;         // 6912 bytes
 constexpr int kMaxCamsPerLaunch = 64;
 
-// Derived bricks: per brick the 9^3 corner voxels [8b, 8b+8] (clamped) of its cells,
-// each as 12 floats = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (mm units), 0, 0:
-// the voxel-wise derivatives of Sec. 2.3, three 16-byte loads per corner.
-constexpr int kDerEdge = 9;
+// Derived bricks: per skip brick the (B+1)^3 corner voxels [Bb, Bb+B] (clamped) of
+// its cells, each as 12 floats = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (mm
+// units), 0, 0: the voxel-wise derivatives of Sec. 2.3, three 16-byte loads per
+// corner (B = 8: 9^3 corners, 34,992 B).
 constexpr int kDerFloats = 12;
-constexpr int kDerBrickFloats = kDerEdge * kDerEdge * kDerEdge * kDerFloats;  // 8748 floats = 34,992 B
+constexpr int kMinBrickShift = 2, kMaxBrickShift = 4;  // skip bricks of 4^3 .. 16^3 cells
+
+__host__ __device__ __forceinline__ int der_edge(int bs) { return (1 << bs) + 1; }
+__host__ __device__ __forceinline__ long long der_brick_floats(int bs) {
+    const long long e = der_edge(bs);
+    return e * e * e * kDerFloats;
+}
+// Per-cell empty bits of a skip brick: B^3 bits, in 32-bit words.
+__host__ __device__ __forceinline__ int cell_words(int bs) { return (1 << (3 * bs)) >> 5; }
 constexpr size_t kDerivedBudgetBytes = (size_t)16 << 30;  // default: built only up to this size
 
 struct CamDev {
@@ -69,14 +81,18 @@ struct VolConst {
 
 struct VolumeDev {
     int n[3];       // voxels per axis
-    int nb[3];      // bricks per axis = ceil((n-1)/8)
+    int nb[3];      // skip bricks per axis = ceil((n-1)/B)
+    int nsb[3];     // storage bricks per axis = ceil((n-1)/8)
+    int bs;         // log2 B, cells per skip-brick edge
+    int der_stride; // floats per derived brick, der_brick_floats(bs)
     float s[3];     // spacing (mm)
-    const float* bricks;     // nbricks * kBrickVox
-    const float* vbricks;    // vesselness bricks (same layout) or nullptr
-    const float* dbricks;    // derived bricks or nullptr (then the per-sample stencils are used)
-    const uint8_t* empty;    // nbricks flags, 1 = skip
-    const uint32_t* cellmask;  // nbricks x 16 words, bit (lz*8+ly)*8+lx set when that cell is empty
-                               // under the current transfer function (nullptr before the precompute)
+    const float* bricks;     // storage bricks x kBrickVox
+    const float* vbricks;    // vesselness storage bricks (same layout) or nullptr
+    const float* dbricks;    // derived skip bricks or nullptr (then the per-sample stencils are used)
+    const uint8_t* empty;    // skip-brick flags, 1 = skip
+    const uint32_t* cellmask;  // skip bricks x cell_words(bs) words, bit (lz*B+ly)*B+lx set when that
+                               // cell is empty under the current transfer function (nullptr before
+                               // the precompute)
     const VolConst* vc;
 };
 
@@ -113,18 +129,26 @@ struct RenderLaunch {
     int W, H, n_cams, cam_offset;
     int skip;
     int packet_w, packet_h;    // ray packet of a warp (packet_w * packet_h == 32); per-lane kernels: 4, 8 or 16 wide
+    int tile_w, tile_h;        // per-lane kernels: CTA tile in pixels (tile_packets_x packets across)
+    int tile_sx;               // log2 of the packets across the tile
     unsigned* work_counter;    // staged kernel work queue (zeroed before launch)
     unsigned* status;          // device status word (kStatusTimeout on an expired wait)
     int n_packets_x, n_packets_y, n_work;
     CamDev cams[kMaxCamsPerLaunch];
 };
 
-// Pixel offset (di, dj) of lane l of warp w within a per-lane kernel's 16 x 8 CTA
-// tile, for warp packets of packet_w x (32 / packet_w) rays, packet_w in {4, 8, 16}.
-__device__ __forceinline__ void tile_pixel(int packet_w, int w, int l, int& di, int& dj) {
+// CTA tile of a per-lane kernel: `warps` warp packets of packet_w x (32 / packet_w)
+// rays (packet_w in {4, 8, 16}), min(warps, 16 / packet_w) packets across and the
+// rest down: 4 warps give 16 x 8 pixels for every packet shape, 2 warps 8 x 8 or
+// 16 x 4, 8 warps 16 x 16.
+__host__ __device__ __forceinline__ int tile_packets_x(int packet_w, int warps) {
+    return warps < 16 / packet_w ? warps : 16 / packet_w;
+}
+
+// Pixel offset (di, dj) of lane l of warp w within that tile (2^sx packets across).
+__device__ __forceinline__ void tile_pixel(int packet_w, int sx, int w, int l, int& di, int& dj) {
     const int pl = __ffs(packet_w) - 1;  // log2 packet_w
-    const int wl = 4 - pl;               // log2 of the warps across the tile
-    const int wx = w & ((1 << wl) - 1), wy = w >> wl;
+    const int wx = w & ((1 << sx) - 1), wy = w >> sx;
     di = (wx << pl) + (l & (packet_w - 1));
     dj = wy * (32 >> pl) + (l >> pl);
 }
@@ -173,17 +197,19 @@ int minmax_blocks(long long n);
 
 cudaError_t launch_normalize(const void* raw, vr_dtype dt, long long n, const float* minmax2, VolConst* vc,
                              float* norm, cudaStream_t st);
+// Storage bricks (8^3 cells) of `nb` storage bricks per axis.
 cudaError_t launch_make_bricks(const float* norm, const int n[3], const int nb[3], float* bricks, cudaStream_t st);
-cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* grid,
+// Skip bricks of 2^bs cells per edge, `nb` per axis.
+cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], int bs, uint16_t* grid,
                                 cudaStream_t st);
-cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], const float s[3], float* dbricks,
-                                cudaStream_t st);
+cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], int bs, const float s[3],
+                                float* dbricks, cudaStream_t st);
 cudaError_t launch_gmax(const float* norm, const int n[3], const float s[3], VolConst* vc, cudaStream_t st);
 cudaError_t launch_classify(const uint16_t* grid, long long nbricks, const float* tf, int tf_w, int tf_h,
                             uint8_t* empty, int* prefix_scratch /* tf_w + 1 ints */, cudaStream_t st);
-constexpr int kCellsPerBrick = kCells * kCells * kCells;  // 512
-cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* cellq, cudaStream_t st);
-cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, const int* prefix, int tf_w,
+cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], int bs, uint16_t* cellq,
+                               cudaStream_t st);
+cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, int bs, const int* prefix, int tf_w,
                                   uint32_t* cellmask, cudaStream_t st);
 
 // Multi-scale vesselness of `norm` into V (both nvox floats); tmp_a and tmp_b are
@@ -200,7 +226,8 @@ cudaError_t launch_tissue_peaks(const unsigned long long* hist, int lo, int hi, 
 cudaError_t launch_median3(const float* in, float* out, const int n[3], cudaStream_t st);
 cudaError_t launch_gauss3d(const float* in, float* out, float* tmp, const int n[3], float sigma, cudaStream_t st);
 
-cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st);
+// warps: warps per CTA (2, 4 or 8), tiled by tile_pixel.
+cudaError_t launch_render_gather(const RenderLaunch& L, int warps, cudaStream_t st);
 cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st);
 // dtf[e] = sum over c of copies[c * n + e]
 cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
@@ -210,7 +237,8 @@ cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStr
 cudaError_t launch_check_probe(unsigned* status, cudaStream_t st);
 cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const float s[3], float* dvol,
                                       cudaStream_t st);
-cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived,
+// bs: the skip-brick size (log2 cells) every view shares, or 0 when they differ.
+cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int ctas, bool all_derived, int bs,
                                 cudaStream_t st);
 cudaError_t batch_ctas_per_sm(int warps_per_block, bool all_derived, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);

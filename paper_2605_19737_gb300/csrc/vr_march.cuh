@@ -11,10 +11,11 @@ struct GlobalLoad {
     __device__ __forceinline__ float operator()(int o) const { return __ldg(p + o); }
 };
 
-// Brick id in 32-bit arithmetic: dims <= 2048 give at most 256^3 = 2^24 bricks.
+// Skip-brick id in 32-bit arithmetic: dims <= 2048 give at most 512^3 = 2^27 bricks.
 __device__ __forceinline__ int brick_index(const VolumeDev& v, const int b[3]) {
     return (b[2] * v.nb[1] + b[1]) * v.nb[0] + b[0];
 }
+
 
 __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, unsigned dense, unsigned evald,
                                              unsigned staged, unsigned shaded, unsigned interp) {
@@ -41,7 +42,11 @@ __device__ __forceinline__ void add_counters(vr_counters* ctr, unsigned rays, un
 // faster that way); the arithmetic, and so the image, is the same.
 // With kState it also returns the ray's last sample index (kstop) and the
 // transmittance in front of that sample (t_last), which the adjoint sweep starts from.
-template <bool kDerived, bool kState = false, bool kParity = false, bool kHessianFirst = true>
+// kBS: log2 of the skip-brick edge in cells, fixed at compile time (2, 3, 4), or 0 to
+// take the volume's at run time (batches that mix sizes); a fixed size keeps the
+// brick and cell index arithmetic in immediates (the run-time form measured 4-10 %
+// slower).
+template <bool kDerived, bool kState = false, bool kParity = false, bool kHessianFirst = true, int kBS = 3>
 __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev& tp, const float4* __restrict__ tf,
                                              const RayDev& r, int skip, float inv_gmax, const float is[3],
                                              float4& out, unsigned& dense, unsigned& evald, unsigned& shaded,
@@ -59,7 +64,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     int cur_bi = -1;
     bool cur_empty = false;
     const float4* dbrick = nullptr;  // derived brick of cur_bi
-    const float* ibrick = nullptr;   // intensity brick of cur_bi
+    const int bs = kBS ? kBS : v.bs, B = 1 << bs, E = B + 1;
     while (k < r.ns) {
         const float kk = (float)k + 0.5f;
         int i0[3], bc[3];
@@ -67,7 +72,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
-            bc[q] = i0[q] >> 3;
+            bc[q] = i0[q] >> bs;
         }
         if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&
                                      (unsigned)bc[2] < (unsigned)v.nb[2])) {
@@ -79,30 +84,30 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             cur_bi = bi;
             if (skip) cur_empty = __ldg(v.empty + bi) != 0;
             if (kDerived)
-                dbrick = reinterpret_cast<const float4*>(v.dbricks) + (size_t)bi * (kDerBrickFloats / 4);
-            else
-                ibrick = v.bricks + (size_t)bi * kBrickVox;
+                dbrick = reinterpret_cast<const float4*>(
+                    v.dbricks + (size_t)bi * (kBS ? (size_t)der_brick_floats(kBS) : (size_t)v.der_stride));
         }
         if (skip && cur_empty) {
-            k = brick_exit_k(r, bc, k, r.ns);
+            k = brick_exit_k(r, bc, B, k, r.ns);
             continue;
         }
-        // local cell of (i0, j0, k0) within the brick: i0 - 8 bc = i0 & 7
-        const int lx = i0[0] & 7, ly = i0[1] & 7, lz = i0[2] & 7;
+        // local cell of (i0, j0, k0) within the skip brick: i0 - B bc = i0 & (B - 1)
+        const int lx = i0[0] & (B - 1), ly = i0[1] & (B - 1), lz = i0[2] & (B - 1);
         if (skip && v.cellmask) {
             // a cell classified empty holds only samples of opacity exactly 0 (their
             // intensity lies in the range of its 8 corners): nothing to read or add
-            const int c = (lz * kCells + ly) * kCells + lx;
-            if ((__ldg(v.cellmask + (size_t)bi * (kCellsPerBrick / 32) + (c >> 5)) >> (c & 31)) & 1u) {
+            const int c = (((lz << bs) + ly) << bs) + lx;
+            if ((__ldg(v.cellmask + (size_t)bi * cell_words(bs) + (c >> 5)) >> (c & 31)) & 1u) {
                 ++ne;
                 ++k;
                 continue;
             }
         }
         ++nip;
-        const int base = (lz * kEdge + ly) * kEdge + lx;
+        int base = 0, sbi = 0;
+        if (!kDerived || v.vbricks) sbi = storage_brick(v, i0, base);
         const float vval =
-            v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)bi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
+            v.vbricks ? value_eval(GlobalLoad{v.vbricks + (size_t)sbi * kBrickVox}, base, f[0], f[1], f[2]) : 0.0f;
         float fld[10], alpha, col[3];
         if (kDerived) {
             // I and the gradient (one 16-byte load per corner) and the Hessian (two), then
@@ -110,8 +115,8 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             // the Hessian, and the sample adds nothing (bit-neutral). The Hessian loads are
             // issued before that test so that they overlap the table lookup (measured:
             // equal at 1080p, 2 % faster on the 8-view workload than loading them after it)
-            derived_channels<kParity, 0, 4>(dbrick, lx, ly, lz, f[0], f[1], f[2], fld);
-            if (kHessianFirst) load_hessian<kParity>(tp, dbrick, lx, ly, lz, f, fld);
+            derived_channels<kParity, 0, 4>(dbrick, E, lx, ly, lz, f[0], f[1], f[2], fld);
+            if (kHessianFirst) load_hessian<kParity>(tp, dbrick, E, lx, ly, lz, f, fld);
             SampleOptics o;
             optics_tf(fld, vval, tp, tf, inv_gmax, o);
             if (o.c.w == 0.0f) {
@@ -119,14 +124,14 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
                 ++k;
                 continue;
             }
-            if (!kHessianFirst) load_hessian<kParity>(tp, dbrick, lx, ly, lz, f, fld);
+            if (!kHessianFirst) load_hessian<kParity>(tp, dbrick, E, lx, ly, lz, f, fld);
             optics_rest(fld, r.dir, tp, o);
             alpha = o.alpha;
             col[0] = o.col[0];
             col[1] = o.col[1];
             col[2] = o.col[2];
         } else {
-            field_eval(GlobalLoad{ibrick}, base, f[0], f[1], f[2], fld);
+            field_eval(GlobalLoad{v.bricks + (size_t)sbi * kBrickVox}, base, f[0], f[1], f[2], fld);
             scale_field(fld, is);
             sample_optics(fld, vval, r.dir, tp, tf, inv_gmax, alpha, col);
         }

@@ -16,17 +16,18 @@ namespace vr {
 
 namespace {
 
-// Resident CTAs per SM: 8 for the derived-brick path (<= 64 registers: equal at 1080p,
-// 2.5 % faster on the 8-view 512^2 workload than 7 at 72 registers), 7 when it also
-// records the ray state (64 registers would spill 64 bytes), 6 for the stencils.
-template <bool kDerived, bool kState>
-__global__ void __launch_bounds__(128, kDerived ? (kState ? 7 : 8) : 6)
+// Registers per thread: 64 for the derived-brick path (8 CTAs of 4 warps per SM:
+// equal at 1080p, 2.5 % faster on the 8-view 512^2 workload than 72), 72 when it also
+// records the ray state (64 would spill 64 bytes), 80 for the stencils. CTAs of 2, 4
+// or 8 warps (tile_pixel).
+template <bool kDerived, bool kState, int kBS>
+__global__ void __launch_bounds__(256, kDerived ? (kState ? 3 : 4) : 3)
     k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
-    tile_pixel(L.packet_w, w, l, di, dj);
-    const int i = blockIdx.x * 16 + di;
-    const int j = blockIdx.y * 8 + dj;
+    tile_pixel(L.packet_w, L.tile_sx, w, l, di, dj);
+    const int i = blockIdx.x * L.tile_w + di;
+    const int j = blockIdx.y * L.tile_h + dj;
     const int cam = blockIdx.z;
     const bool inside = i < L.W && j < L.H;
     const VolumeDev& v = L.vol;
@@ -42,8 +43,8 @@ __global__ void __launch_bounds__(128, kDerived ? (kState ? 7 : 8) : 6)
     int kl = -1;
     float tl = 1.0f;
     if (hit)
-        march_gather<kDerived, kState>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald, shaded, interp, &kl,
-                                       &tl);
+        march_gather<kDerived, kState, false, true, kBS>(v, L.tp, tf, r, L.skip, inv_gmax, is, px, dense, evald,
+                                                         shaded, interp, &kl, &tl);
     if (inside) {
         const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
         reinterpret_cast<float4*>(L.out)[pix] = px;
@@ -58,19 +59,33 @@ __global__ void __launch_bounds__(128, kDerived ? (kState ? 7 : 8) : 6)
 
 }  // namespace
 
-cudaError_t launch_render_gather(const RenderLaunch& L, cudaStream_t st) {
-    dim3 grid((L.W + 15) / 16, (L.H + 7) / 8, L.n_cams);
+template <int kBS>
+void launch_gather_bs(const RenderLaunch& L, dim3 grid, int threads, cudaStream_t st) {
     const bool state = L.ray_state != nullptr;
     if (L.vol.dbricks) {
         if (state)
-            k_render_gather<true, true><<<grid, 128, 0, st>>>(L);
+            k_render_gather<true, true, kBS><<<grid, threads, 0, st>>>(L);
         else
-            k_render_gather<true, false><<<grid, 128, 0, st>>>(L);
+            k_render_gather<true, false, kBS><<<grid, threads, 0, st>>>(L);
     } else {
         if (state)
-            k_render_gather<false, true><<<grid, 128, 0, st>>>(L);
+            k_render_gather<false, true, kBS><<<grid, threads, 0, st>>>(L);
         else
-            k_render_gather<false, false><<<grid, 128, 0, st>>>(L);
+            k_render_gather<false, false, kBS><<<grid, threads, 0, st>>>(L);
+    }
+}
+
+cudaError_t launch_render_gather(const RenderLaunch& L0, int warps, cudaStream_t st) {
+    RenderLaunch L = L0;
+    const int tx = tile_packets_x(L.packet_w, warps);
+    L.tile_w = tx * L.packet_w;
+    L.tile_h = (warps / tx) * L.packet_h;
+    L.tile_sx = __builtin_ctz(tx);
+    dim3 grid((L.W + L.tile_w - 1) / L.tile_w, (L.H + L.tile_h - 1) / L.tile_h, L.n_cams);
+    switch (L.vol.bs) {
+        case 2: launch_gather_bs<2>(L, grid, warps * 32, st); break;
+        case 4: launch_gather_bs<4>(L, grid, warps * 32, st); break;
+        default: launch_gather_bs<3>(L, grid, warps * 32, st); break;
     }
     return cudaGetLastError();
 }
@@ -171,7 +186,7 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
                 }
                 const int bi = (int)brick_index(v, bc);
                 if (L.skip && __ldg(v.empty + bi)) {
-                    k = brick_exit_k(r, bc, k, r.ns);
+                    k = brick_exit_k(r, bc, kCells, k, r.ns);
                 } else {
                     cur = bi;
                 }

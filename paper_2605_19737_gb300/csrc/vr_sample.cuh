@@ -186,7 +186,7 @@ __device__ __forceinline__ void field_eval(const Load& load, int base, float fx,
 
 // Sample field from derived bricks: trilinear interpolation of voxel-wise channels
 // (already in mm units) over the cell's 8 corners; (lx, ly, lz) is the cell's corner
-// voxel (i0, j0, k0) local to the brick's 9^3 block. Channels [kFirst, kFirst +
+// voxel (i0, j0, k0) local to the brick's E^3 block (E = B + 1 corners per edge). Channels [kFirst, kFirst +
 // kCount): kFirst = 0, kCount = 4 reads (I, gx, gy, gz) -- the first 16-byte vector
 // of each corner; kFirst = 4, kCount = 6 the Hessian (Hxx, Hyy, Hzz, Hxy, Hxz, Hyz)
 // -- the second and third. Each channel sums its 8 corners in the same order, so
@@ -209,10 +209,10 @@ __device__ __forceinline__ float4 ldg_l2_256(const float4* p) {
 }
 
 template <bool kParity, int kFirst, int kCount>
-__device__ __forceinline__ void derived_channels(const float4* __restrict__ brick, int lx, int ly, int lz, float fx,
-                                                 float fy, float fz, float* out) {
+__device__ __forceinline__ void derived_channels(const float4* __restrict__ brick, int E, int lx, int ly, int lz,
+                                                 float fx, float fy, float fz, float* out) {
     const int px = kParity ? lx & 1 : 0, py = kParity ? ly & 1 : 0, pz = kParity ? lz & 1 : 0;
-    const int base = (lz * kDerEdge + ly) * kDerEdge + lx;
+    const int base = (lz * E + ly) * E + lx;
 #pragma unroll
     for (int q = 0; q < kCount; ++q) out[q] = 0.0f;
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ __forceinline__ void derived_channels(const float4* __restrict__ bric
         // parity ^ cell parity; otherwise the corner at offset (c & 1, c >> 1 & 1, c >> 2 & 1)
         const int dx = px ^ (c & 1), dy = py ^ ((c >> 1) & 1), dz = pz ^ ((c >> 2) & 1);
         const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-        const float4* p = brick + 3 * (base + (dz * kDerEdge + dy) * kDerEdge + dx);
+        const float4* p = brick + 3 * (base + (dz * E + dy) * E + dx);
         if (kFirst == 0) {
             const float4 a = ldg_l2_256(p);
             out[0] = fmaf(w, a.x, out[0]);
@@ -247,10 +247,10 @@ __device__ __forceinline__ void derived_channels(const float4* __restrict__ bric
 // fma(0, kappa, 1) = 1 for any kappa, and every Hessian gradient carries the factor
 // gamma), so results are unchanged and its 16 loads per sample are saved.
 template <bool kParity>
-__device__ __forceinline__ void load_hessian(const TissueDev& tp, const float4* __restrict__ brick, int lx, int ly,
-                                             int lz, const float f[3], float fld[10]) {
+__device__ __forceinline__ void load_hessian(const TissueDev& tp, const float4* __restrict__ brick, int E, int lx,
+                                             int ly, int lz, const float f[3], float fld[10]) {
     if (tp.gk != 0.0f) {
-        derived_channels<kParity, 4, 6>(brick, lx, ly, lz, f[0], f[1], f[2], fld + 4);
+        derived_channels<kParity, 4, 6>(brick, E, lx, ly, lz, f[0], f[1], f[2], fld + 4);
     } else {
 #pragma unroll
         for (int q = 4; q < 10; ++q) fld[q] = 0.0f;
@@ -402,16 +402,23 @@ __device__ __forceinline__ void scale_field(float f[10], const float is[3]) {
     f[9] *= is[1] * is[2];
 }
 
-// First sample index >= k whose cell lies outside brick (b0, b1, b2), for a ray
-// currently in that brick; a lower bound (one sample earlier is re-tested by
-// the caller), never beyond ns.
-__device__ __forceinline__ int brick_exit_k(const RayDev& r, const int bcell[3], int k, int ns) {
+// Storage brick (8^3 cells) of cell i0 and the offset of its 4-tap stencil origin
+// (voxel i0 - 1 per axis) in the brick's 12^3 block.
+__device__ __forceinline__ int storage_brick(const VolumeDev& v, const int i0[3], int& base) {
+    base = (((i0[2] & 7) * kEdge) + (i0[1] & 7)) * kEdge + (i0[0] & 7);
+    return ((i0[2] >> 3) * v.nsb[1] + (i0[1] >> 3)) * v.nsb[0] + (i0[0] >> 3);
+}
+
+// First sample index >= k whose cell lies outside the skip brick (b0, b1, b2) of B
+// cells per edge, for a ray currently in that brick; a lower bound (one sample
+// earlier is re-tested by the caller), never beyond ns.
+__device__ __forceinline__ int brick_exit_k(const RayDev& r, const int bcell[3], int B, int k, int ns) {
     float kmin = (float)ns;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const float st = r.dhi[q];
         if (st == 0.0f) continue;
-        const float bound = st > 0.0f ? (float)(kCells * (bcell[q] + 1)) : (float)(kCells * bcell[q]);
+        const float bound = st > 0.0f ? (float)(B * (bcell[q] + 1)) : (float)(B * bcell[q]);
         // u(k) = u_n + (k + 1/2) st crosses `bound` at k* = (bound - u_n)/st - 1/2
         const float ks = (bound - r.uhi[q] - r.ulo[q]) / st - 0.5f;
         kmin = fminf(kmin, st > 0.0f ? ceilf(ks) : floorf(ks) + 1.0f);

@@ -157,34 +157,33 @@ __global__ void __launch_bounds__(256) k_make_bricks(const float* __restrict__ n
     }
 }
 
-// One CTA per brick: the voxel-wise intensity, central-difference gradient (Eq. 2)
-// and second/mixed differences (Sec. 2.3) of the brick's 9^3 corner voxels, with
-// clamp-to-edge neighbours, divided by the spacing -- the per-voxel morphology
-// the paper's compute shader produces, laid out for 16-byte loads.
+// One CTA per skip brick: the voxel-wise intensity, central-difference gradient
+// (Eq. 2) and second/mixed differences (Sec. 2.3) of the brick's (B+1)^3 corner
+// voxels, with clamp-to-edge neighbours, divided by the spacing -- the per-voxel
+// morphology the paper's compute shader produces, laid out for 16-byte loads.
 __global__ void __launch_bounds__(256) k_make_derived(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
-                                                      int nby, float hx, float hy, float hz, float* __restrict__ out) {
-    // the brick's corner voxels and their neighbours, [8b - 1, 8b + 10) per axis,
+                                                      int nby, int bs, float hx, float hy, float hz,
+                                                      float* __restrict__ out) {
+    // the brick's corner voxels and their neighbours, [Bb - 1, Bb + B + 2) per axis,
     // clamped to the volume (so neighbour i +- 1 of a corner is tile entry t +- 1)
-    constexpr int kT = kDerEdge + 2;
-    __shared__ float tile[kT * kT * kT];
+    constexpr int kTMax = (1 << kMaxBrickShift) + 3;
+    __shared__ float tile[kTMax * kTMax * kTMax];
+    const int B = 1 << bs, E = B + 1, T = B + 3;
     const long long b = blockIdx.x;
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
-    const int x0 = kCells * bx - 1, y0 = kCells * by - 1, z0 = kCells * bz - 1;
-#pragma unroll
-    for (int q = 0; q < (kT * kT * kT + 255) / 256; ++q) {  // 256 threads: the loads issue back to back
-        const int e = threadIdx.x + 256 * q;
-        if (e >= kT * kT * kT) break;
-        const int tx = e % kT, ty = (e / kT) % kT, tz = e / (kT * kT);
+    const int x0 = B * bx - 1, y0 = B * by - 1, z0 = B * bz - 1;
+    for (int e = threadIdx.x; e < T * T * T; e += blockDim.x) {
+        const int tx = e % T, ty = (e / T) % T, tz = e / (T * T);
         const int x = min(max(x0 + tx, 0), nx - 1), y = min(max(y0 + ty, 0), ny - 1), z = min(max(z0 + tz, 0), nz - 1);
         tile[e] = __ldg(norm + ((long long)z * ny + y) * nx + x);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < kDerEdge * kDerEdge * kDerEdge; e += blockDim.x) {
-        const int lx = e % kDerEdge, ly = (e / kDerEdge) % kDerEdge, lz = e / (kDerEdge * kDerEdge);
+    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+        const int lx = e % E, ly = (e / E) % E, lz = e / (E * E);
         // the corner voxel (clamped as in the per-voxel definition) in tile coordinates
-        const int tx = min(kCells * bx + lx, nx - 1) - x0, ty = min(kCells * by + ly, ny - 1) - y0,
-                  tz = min(kCells * bz + lz, nz - 1) - z0;
-        auto at = [&](int dx, int dy, int dz) { return tile[((tz + dz) * kT + (ty + dy)) * kT + (tx + dx)]; };
+        const int tx = min(B * bx + lx, nx - 1) - x0, ty = min(B * by + ly, ny - 1) - y0,
+                  tz = min(B * bz + lz, nz - 1) - z0;
+        auto at = [&](int dx, int dy, int dz) { return tile[((tz + dz) * T + (ty + dy)) * T + (tx + dx)]; };
         const float c = at(0, 0, 0), c2 = 2.0f * c;
         float4 a, m, t;
         a.x = c;
@@ -199,26 +198,27 @@ __global__ void __launch_bounds__(256) k_make_derived(const float* __restrict__ 
         t.y = ((at(0, 1, 1) - at(0, 1, -1)) - (at(0, -1, 1) - at(0, -1, -1))) * (0.25f * hy * hz);
         t.z = 0.0f;
         t.w = 0.0f;
-        float4* o = reinterpret_cast<float4*>(out + b * kDerBrickFloats) + 3 * e;
+        float4* o = reinterpret_cast<float4*>(out + b * der_brick_floats(bs)) + 3 * e;
         o[0] = a;
         o[1] = m;
         o[2] = t;
     }
 }
 
-// One warp per brick: min/max of I_norm over the brick's corner voxels
-// [8b, min(8b+8, N-1)] per axis, quantised to qlo = floor(min*65535),
+// One warp per skip brick: min/max of I_norm over the brick's corner voxels
+// [Bb, min(Bb+B, N-1)] per axis, quantised to qlo = floor(min*65535),
 // qhi = ceil(max*65535) (float32 round-to-nearest products).
 __global__ void __launch_bounds__(256) k_brick_minmax(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
-                                                      int nby, long long nbricks, uint16_t* __restrict__ grid) {
+                                                      int nby, int bs, long long nbricks, uint16_t* __restrict__ grid) {
     const long long b = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nbricks) return;
+    const int B = 1 << bs;
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
-    const int x0 = kCells * bx, y0 = kCells * by, z0 = kCells * bz;
-    const int ex = min(x0 + kCells, nx - 1) - x0 + 1;
-    const int ey = min(y0 + kCells, ny - 1) - y0 + 1;
-    const int ez = min(z0 + kCells, nz - 1) - z0 + 1;
+    const int x0 = B * bx, y0 = B * by, z0 = B * bz;
+    const int ex = min(x0 + B, nx - 1) - x0 + 1;
+    const int ey = min(y0 + B, ny - 1) - y0 + 1;
+    const int ez = min(z0 + B, nz - 1) - z0 + 1;
     float lo = INFINITY, hi = -INFINITY;
     const int cnt = ex * ey * ez;
     for (int e = lane; e < cnt; e += 32) {
@@ -326,16 +326,20 @@ __global__ void k_classify(const uint16_t* __restrict__ grid, long long nbricks,
     empty[b] = (uint8_t)(prefix[jh + 1] - prefix[jl] == 0);
 }
 
-// Per cell of each brick -- cell (lx, ly, lz) has corner voxels [8b + l, 8b + l + 1]
+// Per cell of each skip brick -- cell (lx, ly, lz) has corner voxels [Bb + l, Bb + l + 1]
 // per axis -- the quantised min/max of I_norm over its 8 corners, with the brick
 // grid's rounding. Cells past the volume's last cell (corner index > N - 2) never
-// hold a sample and get the empty range (65535, 0). One CTA of 512 per brick.
-__global__ void __launch_bounds__(512) k_cell_minmax(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
-                                                     int nby, uint16_t* __restrict__ cellq) {
-    const long long b = blockIdx.x;
+// hold a sample and get the empty range (65535, 0). One thread per cell, cells of a
+// brick consecutive ((lz B + ly) B + lx).
+__global__ void __launch_bounds__(256) k_cell_minmax(const float* __restrict__ norm, int nx, int ny, int nz, int nbx,
+                                                     int nby, int bs, long long ncells, uint16_t* __restrict__ cellq) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ncells) return;
+    const int B = 1 << bs, m = B - 1;
+    const long long b = e >> (3 * bs);
+    const int c = (int)(e & ((1 << (3 * bs)) - 1));
     const int bx = (int)(b % nbx), by = (int)((b / nbx) % nby), bz = (int)(b / ((long long)nbx * nby));
-    const int c = threadIdx.x;
-    const int x = kCells * bx + (c & 7), y = kCells * by + ((c >> 3) & 7), z = kCells * bz + (c >> 6);
+    const int x = B * bx + (c & m), y = B * by + ((c >> bs) & m), z = B * bz + (c >> (2 * bs));
     uint16_t ql = 65535, qh = 0;
     if (x <= nx - 2 && y <= ny - 2 && z <= nz - 2) {
         float lo = INFINITY, hi = -INFINITY;
@@ -345,8 +349,8 @@ __global__ void __launch_bounds__(512) k_cell_minmax(const float* __restrict__ n
         ql = (uint16_t)fminf(fmaxf(floorf(__fmul_rn(lo, 65535.0f)), 0.0f), 65535.0f);
         qh = (uint16_t)fminf(fmaxf(ceilf(__fmul_rn(hi, 65535.0f)), 0.0f), 65535.0f);
     }
-    cellq[2 * (b * kCellsPerBrick + c)] = ql;
-    cellq[2 * (b * kCellsPerBrick + c) + 1] = qh;
+    cellq[2 * e] = ql;
+    cellq[2 * e + 1] = qh;
 }
 
 // A cell is empty under the brick rule applied to its own range: no transfer-function
@@ -356,7 +360,8 @@ __global__ void __launch_bounds__(512) k_cell_minmax(const float* __restrict__ n
 __global__ void __launch_bounds__(256) k_classify_cells(const uint16_t* __restrict__ cellq, long long ncells,
                                                         const int* __restrict__ prefix, int w,
                                                         uint32_t* __restrict__ cellmask) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // ncells is a multiple of 512
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((e & ~31ll) >= ncells) return;  // ncells is a multiple of 64: warps are whole
     const long long ql = cellq[2 * e], qh = cellq[2 * e + 1];
     bool empty = true;
     if (ql <= qh) {
@@ -368,21 +373,22 @@ __global__ void __launch_bounds__(256) k_classify_cells(const uint16_t* __restri
     }
     const unsigned bits = __ballot_sync(0xffffffffu, empty);
     if ((threadIdx.x & 31) == 0) cellmask[e >> 5] = bits;
-    (void)ncells;
 }
 
 }  // namespace
 
-cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* cellq, cudaStream_t st) {
-    const long long nbr = (long long)nb[0] * nb[1] * nb[2];
-    k_cell_minmax<<<(unsigned)nbr, kCellsPerBrick, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], cellq);
+cudaError_t launch_cell_minmax(const float* norm, const int n[3], const int nb[3], int bs, uint16_t* cellq,
+                               cudaStream_t st) {
+    const long long ncells = ((long long)nb[0] * nb[1] * nb[2]) << (3 * bs);
+    k_cell_minmax<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], bs, ncells,
+                                                                    cellq);
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, const int* prefix, int tf_w,
+cudaError_t launch_classify_cells(const uint16_t* cellq, long long nbricks, int bs, const int* prefix, int tf_w,
                                   uint32_t* cellmask, cudaStream_t st) {
-    const long long ncells = nbricks * kCellsPerBrick;
-    k_classify_cells<<<(unsigned)(ncells / 256), 256, 0, st>>>(cellq, ncells, prefix, tf_w, cellmask);
+    const long long ncells = nbricks << (3 * bs);
+    k_classify_cells<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(cellq, ncells, prefix, tf_w, cellmask);
     return cudaGetLastError();
 }
 
@@ -423,19 +429,19 @@ cudaError_t launch_make_bricks(const float* norm, const int n[3], const int nb[3
     return cudaGetLastError();
 }
 
-cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], uint16_t* grid,
+cudaError_t launch_brick_minmax(const float* norm, const int n[3], const int nb[3], int bs, uint16_t* grid,
                                 cudaStream_t st) {
     const long long nbr = (long long)nb[0] * nb[1] * nb[2];
     const unsigned blocks = (unsigned)((nbr + 7) / 8);
-    k_brick_minmax<<<blocks, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], nbr, grid);
+    k_brick_minmax<<<blocks, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], bs, nbr, grid);
     return cudaGetLastError();
 }
 
-cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], const float s[3], float* dbricks,
-                                cudaStream_t st) {
+cudaError_t launch_make_derived(const float* norm, const int n[3], const int nb[3], int bs, const float s[3],
+                                float* dbricks, cudaStream_t st) {
     const long long nbr = (long long)nb[0] * nb[1] * nb[2];
-    k_make_derived<<<(unsigned)nbr, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], 1.0f / s[0], 1.0f / s[1],
-                                                  1.0f / s[2], dbricks);
+    k_make_derived<<<(unsigned)nbr, 256, 0, st>>>(norm, n[0], n[1], n[2], nb[0], nb[1], bs, 1.0f / s[0],
+                                                  1.0f / s[1], 1.0f / s[2], dbricks);
     return cudaGetLastError();
 }
 

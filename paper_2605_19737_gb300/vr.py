@@ -78,6 +78,7 @@ SIGNATURES = {
     "vr_set_normalized": ([_P, _I, _P], _I),
     "vr_get_bricks": ([_P, _I, _P, _P, _P], _I),
     "vr_get_layout": ([_P, _I, _P, _P, _P], _I),
+    "vr_set_brick_size": ([_P, _I, _I], _I),
     "vr_get_vesselness": ([_P, _I, _P, _I], _I),
     "vr_load_second_channel": ([_P, _I, _P, _I, _I], _I),
     "vr_get_normalized": ([_P, _I, _P, _I], _I),

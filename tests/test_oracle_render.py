@@ -147,44 +147,58 @@ def test_early_termination_bound():
     assert np.all(d[..., :3] <= rem * cmax + 1e-12)
 
 
-def test_brick_quantisation_matches_numpy_float32():
-    """Brick (qlo, qhi): an independent numpy float32 statement of the definition, bit for bit."""
+@pytest.mark.parametrize("B", [4, 8, 16])
+def test_brick_quantisation_matches_numpy_float32(B):
+    """Brick (qlo, qhi) for bricks of B^3 cells: an independent numpy float32 statement
+    of the definition (corner voxels [Bb, Bb + B] per axis), bit for bit."""
     for vol in (ph.random_volume((19, 17, 10), 17, np.float32),
-                ph.random_volume((20, 9, 18), 18, np.uint16)):
-        g = oracle.brick_minmax_q(vol)
+                ph.random_volume((20, 9, 18), 18, np.uint16), ph.random_volume((37, 21, 34), 19, np.float32)):
+        g = oracle.brick_minmax_q(vol, brick=B)
         v32 = vol.astype(np.float32)
         lo, hi = v32.min(), v32.max()
         r = (v32 - lo) / np.float32(hi - lo)  # float32 ops, round-to-nearest
         nz, ny, nx = vol.shape
+        assert g.shape[:3] == tuple(-(-(n - 1) // B) for n in (nz, ny, nx))
         for bz in range(g.shape[0]):
             for by in range(g.shape[1]):
                 for bx in range(g.shape[2]):
-                    blk = r[8 * bz:8 * bz + 9, 8 * by:8 * by + 9, 8 * bx:8 * bx + 9]
+                    blk = r[B * bz:B * bz + B + 1, B * by:B * by + B + 1, B * bx:B * bx + B + 1]
                     assert g[bz, by, bx, 0] == int(np.floor(blk.min() * np.float32(65535)))
                     assert g[bz, by, bx, 1] == int(np.ceil(blk.max() * np.float32(65535)))
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_skip_classification_is_conservative(mode):
+def test_brick_grids_nest():
+    """A brick of 2B cells is the union of 8 bricks of B cells (their corner ranges
+    overlap on shared faces), so its range is the hull of theirs."""
+    vol = ph.random_volume((37, 29, 33), 23, np.float32)
+    for B in (4, 8):
+        fine, coarse = oracle.brick_minmax_q(vol, brick=B), oracle.brick_minmax_q(vol, brick=2 * B)
+        for bz, by, bx in np.ndindex(*coarse.shape[:3]):
+            sub = fine[2 * bz:2 * bz + 2, 2 * by:2 * by + 2, 2 * bx:2 * bx + 2]
+            assert coarse[bz, by, bx, 0] == sub[..., 0].min() and coarse[bz, by, bx, 1] == sub[..., 1].max()
+
+
+@pytest.mark.parametrize("mode,B", [(0, 8), (1, 8), (0, 4), (1, 16)])
+def test_skip_classification_is_conservative(mode, B):
     """Brute force: any point with alpha > 0 (dense 3-per-voxel grid, plus voxel centres)
     lies in a brick classified non-empty; and some bricks are empty."""
-    vol = ph.head_phantom((26, 20, 18), seed=19)
+    vol = ph.head_phantom((26, 20, 18) if B < 16 else (50, 42, 38), seed=19)
     sp = (1.0, 1.0, 1.0)
     In = oracle.normalize(vol)
     tf1 = ph.tf_1d_windows(ph.HEAD_WINDOWS, {"csf": 0.05, "gm": 0.1, "wm": 0.2}, ramp=0.03)
     tf = tf1 if mode == 0 else ph.tf_2d_gradient(tf1)
     h = tf.shape[0]
-    grid = oracle.brick_minmax_q(vol)
+    grid = oracle.brick_minmax_q(vol, brick=B)
     empty = oracle.classify(grid, tf)
     assert empty.sum() > 0 and (1 - empty).sum() > 0
     P = oracle.make_params(tf_mode=mode, tf_shape=(h, 256), grad_mod=1, shading=0, gamma=0.5, kappa_ref=0.05)
-    dims = np.array([26, 20, 18])
+    dims = np.array(vol.shape[::-1])
     u = [np.arange(0, n - 1 + 1e-9, 1.0 / 3.0) for n in dims]
     U = np.stack(np.meshgrid(*u, indexing="ij"), -1).reshape(-1, 3)
     pts = (U + 0.5) * np.asarray(sp)
     out = oracle.sample_points(In, sp, P, tf, pts, np.array([0.0, 0.0, 1.0]))
     i0 = np.minimum(np.floor(U).astype(int), dims - 2)
-    b = i0 // 8
+    b = i0 // B
     bflat = (b[:, 2] * empty.shape[1] + b[:, 1]) * empty.shape[2] + b[:, 0]
     visible = out[:, 0] > 0
     assert visible.sum() > 0
