@@ -908,7 +908,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     // (vector atomics), then one gather pass applies the channels' stencil transposes.
     const bool channels = d_dvolume && B.r.vol.dbricks;
     if (channels) {
-        const size_t need = sizeof(float) * kDerFloats * (size_t)v->nvox;
+        const size_t need = sizeof(float) * 10 * (size_t)v->nvox;  // three channel planes
         if (ctx->dgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
             dfree(ctx, ctx->d_dgrad);

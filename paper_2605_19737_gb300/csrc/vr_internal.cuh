@@ -161,7 +161,8 @@ struct BackwardLaunch {
     float* dvol;            // nvox or nullptr, zeroed by the caller
     float* dtf_copies;      // n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
     int n_copies;
-    float* dgrad;           // derived-brick path with dvol: zeroed nvox x kDerFloats channel gradients, else nullptr
+    float* dgrad;           // derived-brick path with dvol: zeroed channel gradients (10 floats per voxel
+                            // in three planes, chan_index), else nullptr
 };
 
 // One view of a batched render (device-resident table).
