@@ -116,8 +116,10 @@ typedef enum {
                               derivatives precomputed by vr_precompute_morphology (8 corners per
                               sample) when they fit the memory budget, else as GATHER_STENCIL */
     VR_KERNEL_STAGED = 2,  /* warp-cooperative brick staging in shared memory, per-sample stencils */
-    VR_KERNEL_GATHER_STENCIL = 3  /* per-lane reads, per-sample stencils over the 56 weighted voxels
+    VR_KERNEL_GATHER_STENCIL = 3, /* per-lane reads, per-sample stencils over the 56 weighted voxels
                                      of the cell's 4x4x4 neighbourhood (no derived data) */
+    VR_KERNEL_STAGED_DERIVED = 4  /* warp-cooperative staging of derived skip bricks (4^3 or 8^3
+                                     cells) in shared memory by bulk copy; no second channel */
 } vr_kernel;
 
 typedef struct {

@@ -354,7 +354,8 @@ static void sample_optics_k(const or_vol *v, const or_params *P, const double *t
          * quantity, from worst-case rounding bounds (u = 2^-24 per IEEE operation;
          * the interpolated values are sums of 8 products with rounded trilinear
          * weights, the voxel-wise derivatives are rounded differences of the same
-         * float32 voxels, the sample position is good to 3e-8 voxel). A knot counts
+         * float32 voxels, the sample position is good to 2e-7 voxel: 32.32 fixed
+         * point over up to ~1600 samples per ray). A knot counts
          * only where the table actually bends; exact zeros and ends (I = 0 or 1) are
          * exact in float32 too and are not flagged. */
         const double u = 5.9604644775390625e-8;
@@ -363,11 +364,11 @@ static void sample_optics_k(const or_vol *v, const or_params *P, const double *t
         const double smin = fmin(v->s[0], fmin(v->s[1], v->s[2]));
         const int w_ = P->tf_w, h_ = P->tf_h;
         const double xs = clampd(fld[0], 0.0, 1.0) * (w_ - 1);
-        const double wx = (w_ - 1) * u * (12.0 * fabs(fld[0]) + M);
+        const double wx = (w_ - 1) * u * (12.0 * fabs(fld[0]) + 4.0 * M);
         double ys = 0.0, wy = 0.0;
         if (h_ > 1) {
             ys = clampd(y, 0.0, 1.0) * (h_ - 1);
-            wy = P->tf_mode == 1 ? (h_ - 1) * (33.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn)
+            wy = P->tf_mode == 1 ? (h_ - 1) * (40.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn)
                                  : (h_ - 1) * 10.0 * u * Vm;
         }
         const int jl = (int)fmin(floor(xs), w_ - 2), kl = h_ > 1 ? (int)fmin(floor(ys), h_ - 2) : 0;
@@ -382,7 +383,7 @@ static void sample_optics_k(const or_vol *v, const or_params *P, const double *t
         }
         /* |g|/gmax; kappa (its voxel Hessians are rounded second differences, and the
          * gradient's rounding enters through dkappa/dg = 2 (H g - kappa g) / |g|^2) */
-        const double dgn = 33.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn;
+        const double dgn = 40.0 * u * (v->gmax > 0.0 ? G / v->gmax : 0.0) + 3.0 * u * gn;
         double dwin = 0.0;
         if (P->gamma != 0.0 && gg > 0.0) {
             const double dk = 24.0 * u * M / (smin * smin) + 42.0 * u * Hm +

@@ -14,7 +14,7 @@ import numpy as np
 from . import vr as _vr
 from .vr import (  # noqa: F401
     VR_F32, VR_U16, VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL,
-    VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL,
+    VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL, VR_KERNEL_STAGED_DERIVED,
     vr_camera, vr_tissue_params, vr_counters, vr_render_opts, vr_view,
 )
 

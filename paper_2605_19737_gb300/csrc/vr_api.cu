@@ -803,7 +803,21 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     if (!v->params_ready) return fail(ctx, VR_ERR_NOT_READY, "render: call vr_set_tissue_params first");
     vr_render_opts o{VR_KERNEL_AUTO, 1, 4, 4, nullptr};
     if (opts) o = *opts;
-    if (o.kernel < 0 || o.kernel > 3) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
+    if (o.kernel < 0 || o.kernel > 4) return fail(ctx, VR_ERR_INVALID_ARG, "render: bad kernel choice");
+    const bool staged_der = o.kernel == VR_KERNEL_STAGED_DERIVED;
+    if (staged_der) {
+        if (!v->d_dbricks)
+            return fail(ctx, VR_ERR_INVALID_ARG, "render: the staged derived kernel needs the derived bricks");
+        if (v->bs > 3)
+            return fail(ctx, VR_ERR_INVALID_ARG, "render: the staged derived kernel stages 4^3- or 8^3-cell bricks");
+        if (v->tp.tf_mode == 2)
+            return fail(ctx, VR_ERR_INVALID_ARG, "render: the staged derived kernel has no second channel");
+        if (o.ray_state) return fail(ctx, VR_ERR_INVALID_ARG, "render: ray_state needs a per-lane kernel");
+        if (o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16 && o.packet_w != 32)
+            return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8, 16 or 32");
+        if (o.warps_per_block < 1 || o.warps_per_block > (v->bs == 2 ? 8 : 6))
+            return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block outside the shared memory of a CTA");
+    }
     if (o.kernel == VR_KERNEL_STAGED && o.ray_state)
         return fail(ctx, VR_ERR_INVALID_ARG, "render: ray_state needs a per-lane kernel");
     // VR_KERNEL_AUTO picks the per-lane gather kernel: on GB300 the bricked volume stays
@@ -816,9 +830,9 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         return fail(ctx, VR_ERR_INVALID_ARG, "render: the staged kernel stages 8^3-cell bricks (vr_set_brick_size 8)");
     if (staged && (o.warps_per_block < 1 || o.warps_per_block > 8))
         return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be in [1, 8]");
-    if (!staged && o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16)
+    if (!staged && !staged_der && o.packet_w != 4 && o.packet_w != 8 && o.packet_w != 16)
         return fail(ctx, VR_ERR_INVALID_ARG, "render: packet_w must be 4, 8 or 16 for the per-lane kernels");
-    if (!staged && o.warps_per_block != 2 && o.warps_per_block != 4 && o.warps_per_block != 8)
+    if (!staged && !staged_der && o.warps_per_block != 2 && o.warps_per_block != 4 && o.warps_per_block != 8)
         return fail(ctx, VR_ERR_INVALID_ARG, "render: warps_per_block must be 2, 4 or 8 for the per-lane kernels");
     DeviceGuard g(ctx->device);
     float* dst = out_rgba;
@@ -841,6 +855,14 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     L.n_packets_x = (W + L.packet_w - 1) / L.packet_w;
     L.n_packets_y = (H + L.packet_h - 1) / L.packet_h;
     int ctas = 0;
+    if (staged_der) {
+        int per_sm = 0;
+        CK(staged_derived_config(o.warps_per_block, v->bs, &per_sm), "render: staged derived kernel configuration");
+        if (per_sm < 1) return fail(ctx, VR_ERR_INVALID_ARG, "render: staged derived kernel does not fit on an SM");
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "render: SM count");
+        ctas = sms * per_sm;
+    }
     if (staged) {
         const bool ves = L.vol.vbricks != nullptr;
         int& per_sm = ctx->staged_ctas[ves][o.warps_per_block];
@@ -855,11 +877,16 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
         L.n_cams = nc;
         L.cam_offset = c0;
         memcpy(L.cams, h_cams + c0, sizeof(CamDev) * nc);
-        if (staged) {
+        if (staged || staged_der) {
             L.n_work = nc * L.n_packets_x * L.n_packets_y;
             const int need = (L.n_work + o.warps_per_block - 1) / o.warps_per_block;
             CK(cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned), ctx->stream), "render: reset work counter");
-            CK(launch_render_staged(L, o.warps_per_block, ctas < need ? ctas : need, ctx->stream), "render kernel");
+            if (staged_der)
+                CK(launch_render_staged_derived(L, o.warps_per_block, ctas < need ? ctas : need, ctx->stream),
+                   "render kernel");
+            else
+                CK(launch_render_staged(L, o.warps_per_block, ctas < need ? ctas : need, ctx->stream),
+                   "render kernel");
         } else {
             CK(launch_render_gather(L, o.warps_per_block, ctx->stream), "render kernel");
         }

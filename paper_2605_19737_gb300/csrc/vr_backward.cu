@@ -228,12 +228,11 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
             float A = 0.f, A_prev = 0.f;
             int k = 0, klast = -1;
             while (k < r.ns) {
-                const float kk = (float)k + 0.5f;
                 int i0[3], bc[3];
                 float f[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    sample_cell(r, q, k, v.n[q], i0[q], f[q]);
                     bc[q] = i0[q] >> kBS;
                 }
                 if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
@@ -276,12 +275,11 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
             const int kmax = __reduce_max_sync(0xffffffffu, kstop);
             for (int kr = kmax; kr >= 0; --kr) {
                 if (kr > kstop) continue;
-                const float kk = (float)kr + 0.5f;
                 int i0[3], bc[3];
                 float f[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    sample_cell(r, q, kr, v.n[q], i0[q], f[q]);
                     bc[q] = i0[q] >> kBS;
                 }
                 // No skipping here: a sample in an empty brick has alpha = 0, but its lookup
@@ -431,12 +429,11 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
         int k = 0, klast = -1;
         kstop = r.ns - 1;
         while (k < r.ns) {
-            const float kk = (float)k + 0.5f;
             int i0[3], bc[3];
             float f[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                sample_cell(r, q, k, v.n[q], i0[q], f[q]);
                 bc[q] = i0[q] >> 3;
             }
             if (!VR_CHECK(L.tp.status, (unsigned)i0[0] <= (unsigned)(v.n[0] - 2) &&
@@ -475,10 +472,9 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
         int i0[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
         float f[3] = {0.f, 0.f, 0.f};
         if (live) {
-            const float kk = (float)kr + 0.5f;
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                sample_cell(r, q, kr, v.n[q], i0[q], f[q]);
                 bc[q] = i0[q] >> 3;
             }
         }
@@ -532,11 +528,10 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
                     live = false;
                     break;
                 }
-                const float kk = (float)kr + 0.5f;
                 int b2[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                    sample_cell(r, q, kr, v.n[q], i0[q], f[q]);
                     b2[q] = i0[q] >> 3;
                 }
                 if (b2[0] != sc[0] || b2[1] != sc[1] || b2[2] != sc[2]) break;

@@ -243,6 +243,10 @@ cudaError_t launch_render_batch(const BatchLaunch& B, int warps_per_block, int c
                                 cudaStream_t st);
 cudaError_t batch_ctas_per_sm(int warps_per_block, bool all_derived, int* per_sm);
 cudaError_t launch_render_staged(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
+// The staged design on the derived bricks (skip bricks of 4^3 or 8^3 cells, bs 2 or 3).
+cudaError_t launch_render_staged_derived(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st);
+int staged_derived_smem_bytes(int warps_per_block, int bs);
+cudaError_t staged_derived_config(int warps_per_block, int bs, int* ctas_per_sm);
 int staged_smem_bytes(int warps_per_block, bool vessel);
 // Set the kernel's dynamic shared-memory limit and report resident CTAs per SM.
 cudaError_t staged_config(int warps_per_block, bool vessel, int* ctas_per_sm);

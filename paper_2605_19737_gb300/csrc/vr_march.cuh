@@ -66,12 +66,11 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     const float4* dbrick = nullptr;  // derived brick of cur_bi
     const int bs = kBS ? kBS : v.bs, B = 1 << bs, E = B + 1;
     while (k < r.ns) {
-        const float kk = (float)k + 0.5f;
         int i0[3], bc[3];
         float f[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+            sample_cell(r, q, k, v.n[q], i0[q], f[q]);
             bc[q] = i0[q] >> bs;
         }
         if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&

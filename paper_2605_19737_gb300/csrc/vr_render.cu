@@ -170,12 +170,11 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
                     live = false;
                     break;
                 }
-                const float kk = (float)k + 0.5f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     int i0;
                     float f;
-                    sample_cell(r, q, kk, v.n[q], i0, f);
+                    sample_cell(r, q, k, v.n[q], i0, f);
                     bc[q] = i0 >> 3;
                 }
                 if (!VR_CHECK(L.tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] &&
@@ -222,12 +221,11 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
 
             if (live && cur == sel) {
                 while (true) {
-                    const float kk = (float)k + 0.5f;
                     int i0[3], b2[3];
                     float f[3];
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        sample_cell(r, q, kk, v.n[q], i0[q], f[q]);
+                        sample_cell(r, q, k, v.n[q], i0[q], f[q]);
                         b2[q] = i0[q] >> 3;
                     }
                     if (b2[0] != sc[0] || b2[1] != sc[1] || b2[2] != sc[2]) {
@@ -282,7 +280,221 @@ __global__ void __launch_bounds__(256) k_render_staged(const __grid_constant__ R
     if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u, eval_tot, eval_tot);
 }
 
+// k_render_staged_derived: the staged design on the derived bricks. Persistent
+// warps pull packets as k_render_staged does; each warp keeps one derived skip brick
+// ((B+1)^3 corners x 48 B: 6000 B for B = 4, 34,992 B for B = 8) in shared memory.
+// Every round each live lane advances to its next sample outside empty bricks, the
+// warp picks the front-most brick any live lane needs, one lane pulls it in with a
+// bulk copy completing on an mbarrier (bounded wait), and the lanes whose next sample
+// lies in it march through it reading the 8 corners of their cells from shared
+// memory (cell bits and the transfer function still through L1). The warp leaves
+// when a vote finds no live lane. Each lane walks its own samples front to back with
+// the gather kernel's arithmetic (offset-order corner sums), so the image is the
+// same bit for bit. No vesselness channel (mode 2 uses the gather kernels).
+template <int kBS>
+__global__ void __launch_bounds__(256, 3) k_render_staged_derived(const __grid_constant__ RenderLaunch L) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int B = 1 << kBS, E = B + 1;
+    constexpr int kFloats = E * E * E * kDerFloats;
+    constexpr unsigned kBytes = kFloats * 4;  // a multiple of 16
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* my = smem_raw + (size_t)warp * (kBytes + 128);
+    const float4* sbrick = reinterpret_cast<const float4*>(my);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(my + kBytes);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    unsigned parity = 0;
+    bool failed = false;
+    const VolumeDev& v = L.vol;
+    const TissueDev& tp = L.tp;
+    const float4* tf = reinterpret_cast<const float4*>(L.tf);
+    const float gmax = __ldg(&v.vc->gmax);
+    const float inv_gmax = gmax > 0.0f ? 1.0f / gmax : 0.0f;
+    const int ppx = L.packet_w, ppy = L.packet_h;
+    unsigned staged = 0, rays_hit = 0, dense_tot = 0, eval_tot = 0, shade_tot = 0, interp_tot = 0;
+
+    while (!failed) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(L.work_counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned)L.n_work) break;
+        const int px = item % L.n_packets_x;
+        const int py = (item / L.n_packets_x) % L.n_packets_y;
+        const int cam = item / (L.n_packets_x * L.n_packets_y);
+        const int i = px * ppx + lane % ppx, j = py * ppy + lane / ppx;
+        const bool inside = i < L.W && j < L.H;
+        const CamDev& cd = L.cams[cam];
+        int eb[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) eb[q] = (int)floorf((cd.eye[q] / v.s[q] - 0.5f) / (float)B);
+        RayDev r;
+        bool live = inside && setup_ray(cd, L.rc, i, j, v.n, v.s, r);
+        const bool hit = live;
+        int k = 0, kstop = -1, cur = -1, bc[3] = {0, 0, 0};
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+        unsigned ne = 0, nsh = 0, nip = 0;
+        while (true) {
+            while (live && cur < 0) {  // this lane's next sample outside empty bricks
+                if (k >= r.ns) {
+                    live = false;
+                    break;
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    int i0;
+                    float f;
+                    sample_cell(r, q, k, v.n[q], i0, f);
+                    bc[q] = i0 >> kBS;
+                }
+                if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&
+                                             (unsigned)bc[2] < (unsigned)v.nb[2])) {
+                    live = false;
+                    break;
+                }
+                const int bi = brick_index(v, bc);
+                if (L.skip && __ldg(v.empty + bi))
+                    k = brick_exit_k(r, bc, B, k, r.ns);
+                else
+                    cur = bi;
+            }
+            const unsigned key = live ? brick_key(bc, eb) : 0xffffffffu;
+            const unsigned mk = __reduce_min_sync(0xffffffffu, key);
+            if (mk == 0xffffffffu) break;  // warp vote: no live lane left
+            const int leader = __ffs(__ballot_sync(0xffffffffu, key == mk)) - 1;
+            const int sel = __shfl_sync(0xffffffffu, cur, leader);
+            int sc[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sc[q] = __shfl_sync(0xffffffffu, bc[q], leader);
+            __syncwarp();  // every lane is done reading the previous brick
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, kBytes);
+                bulk_g2s(my, v.dbricks + (size_t)sel * kFloats, kBytes, bar);
+                ++staged;
+            }
+            const bool arrived = __all_sync(0xffffffffu, mbar_wait_bounded(bar, parity));
+            if (!arrived) {
+                (void)mbar_wait_bounded(bar, parity);  // nothing in flight when the warp leaves
+                failed = true;
+                if (lane == 0) atomicOr(L.status, kStatusTimeout);
+                break;
+            }
+            parity ^= 1u;
+            if (live && cur == sel) {
+                while (true) {
+                    int i0[3], b2[3];
+                    float f[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        sample_cell(r, q, k, v.n[q], i0[q], f[q]);
+                        b2[q] = i0[q] >> kBS;
+                    }
+                    if (b2[0] != sc[0] || b2[1] != sc[1] || b2[2] != sc[2]) {
+                        cur = -1;
+                        break;
+                    }
+                    const int lx = i0[0] & (B - 1), ly = i0[1] & (B - 1), lz = i0[2] & (B - 1);
+                    bool done_sample = false;
+                    if (L.skip && v.cellmask) {
+                        const int c = (((lz << kBS) + ly) << kBS) + lx;
+                        if ((__ldg(v.cellmask + (size_t)sel * cell_words(kBS) + (c >> 5)) >> (c & 31)) & 1u)
+                            done_sample = true;
+                    }
+                    if (!done_sample) {
+                        ++nip;
+                        float fld[10];
+                        derived_channels_smem<0, 4>(sbrick, E, lx, ly, lz, f[0], f[1], f[2], fld);
+                        if (tp.gk != 0.0f) {
+                            derived_channels_smem<4, 6>(sbrick, E, lx, ly, lz, f[0], f[1], f[2], fld + 4);
+                        } else {
+#pragma unroll
+                            for (int q = 4; q < 10; ++q) fld[q] = 0.0f;
+                        }
+                        SampleOptics o;
+                        optics_tf(fld, 0.0f, tp, tf, inv_gmax, o);
+                        if (o.c.w != 0.0f) {
+                            optics_rest(fld, r.dir, tp, o);
+                            ++nsh;
+                            const float wgt = (1.0f - A) * o.alpha;  // Eqs. 5-6
+                            C0 = fmaf(o.col[0], wgt, C0);
+                            C1 = fmaf(o.col[1], wgt, C1);
+                            C2 = fmaf(o.col[2], wgt, C2);
+                            A += wgt;
+                        }
+                    }
+                    ++ne;
+                    if (A >= tp.et_threshold) {
+                        kstop = k;
+                        live = false;
+                        break;
+                    }
+                    if (++k >= r.ns) {
+                        live = false;
+                        break;
+                    }
+                }
+            }
+        }
+        if (failed) break;
+        const unsigned dense = hit ? (kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns) : 0u;
+        if (inside) {
+            const long long pix = ((long long)(L.cam_offset + cam) * L.H + j) * L.W + i;
+            reinterpret_cast<float4*>(L.out)[pix] = make_float4(C0, C1, C2, A);
+            if (L.ray_samples) {
+                L.ray_samples[2 * pix] = dense;
+                L.ray_samples[2 * pix + 1] = ne;
+            }
+        }
+        rays_hit += hit ? 1u : 0u;
+        dense_tot += dense;
+        eval_tot += ne;
+        shade_tot += nsh;
+        interp_tot += nip;
+    }
+    if (L.counters) add_counters(L.counters, rays_hit, dense_tot, eval_tot, lane == 0 ? staged : 0u, shade_tot,
+                                 interp_tot);
+}
+
+template <int kBS>
+int staged_derived_bytes() {
+    constexpr int E = (1 << kBS) + 1;
+    return E * E * E * kDerFloats * 4 + 128;
+}
+
 }  // namespace
+
+int staged_derived_smem_bytes(int warps_per_block, int bs) {
+    return warps_per_block * (bs == 2 ? staged_derived_bytes<2>() : staged_derived_bytes<3>());
+}
+
+cudaError_t staged_derived_config(int warps_per_block, int bs, int* ctas_per_sm) {
+    const int smem = staged_derived_smem_bytes(warps_per_block, bs);
+    cudaError_t e;
+    if (bs == 2) {
+        e = cudaFuncSetAttribute(k_render_staged_derived<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 staged_derived_smem_bytes(8, 2));
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_render_staged_derived<2>,
+                                                             warps_per_block * 32, smem);
+    }
+    e = cudaFuncSetAttribute(k_render_staged_derived<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             staged_derived_smem_bytes(6, 3));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_render_staged_derived<3>, warps_per_block * 32,
+                                                         smem);
+}
+
+cudaError_t launch_render_staged_derived(const RenderLaunch& L, int warps_per_block, int ctas, cudaStream_t st) {
+    const int smem = staged_derived_smem_bytes(warps_per_block, L.vol.bs);
+    if (L.vol.bs == 2)
+        k_render_staged_derived<2><<<ctas, warps_per_block * 32, smem, st>>>(L);
+    else
+        k_render_staged_derived<3><<<ctas, warps_per_block * 32, smem, st>>>(L);
+    return cudaGetLastError();
+}
 
 int staged_smem_bytes(int warps_per_block, bool vessel) {
     return warps_per_block * ((vessel ? 2 : 1) * kBrickBytes + 128);

@@ -23,13 +23,28 @@
 namespace vr {
 
 struct RayDev {
-    int ns;           // number of samples t_k = t_near + (k+1/2) dt < t_far
-    float uhi[3];     // voxel coordinate at t_near: head
-    float ulo[3];     //                             tail
-    float dhi[3];     // voxel-coordinate step per sample: head
-    float dlo[3];     //                                   tail
-    float dir[3];     // unit ray direction
+    int ns;             // number of samples t_k = t_near + (k+1/2) dt < t_far
+    long long u0[3];    // voxel coordinate of sample 0 (t_near + dt/2), 32.32 fixed point
+    long long du[3];    // voxel-coordinate step per sample, 32.32 fixed point
+    float dir[3];       // unit ray direction
 };
+
+// 32.32 fixed point from a double-float x (|x| < 2^30), with 32-bit conversions only
+// (64-bit float<->integer conversions are slow on this part): the head's whole part
+// (truncated), its fraction h - trunc(h) -- exact, h and trunc(h) share sign and
+// binade or trunc(h) = 0 -- scaled by 2^31 and doubled (2^-32 resolution), and the
+// tail scaled by 2^32.
+__device__ __forceinline__ long long df_to_fx(dfloat x) {
+    const float t = truncf(x.hi);
+    const long long whole = (long long)__float2int_rz(t) << 32;
+    const long long frac = 2 * (long long)__float2int_rn((x.hi - t) * 2147483648.0f);
+    return whole + frac + (long long)__float2int_rn(x.lo * 4294967296.0f);
+}
+
+// A 32.32 fixed-point value as float (|U| < 2^62), again without 64-bit conversions.
+__device__ __forceinline__ float fx_to_float(long long U) {
+    return fmaf(__uint2float_rn((unsigned)U), 2.3283064365386963e-10f, (float)(int)(U >> 32));
+}
 
 // Ray through pixel (i, j): direction normalize(fwd + a right + b up),
 // a = 2(i+1/2)/W - 1, b = 1 - 2(j+1/2)/H; slab intersection with the volume box;
@@ -81,39 +96,31 @@ __device__ __forceinline__ bool setup_ray(const CamDev& c, const RayConsts& rc, 
     for (int q = 0; q < 3; ++q) {
         const dfloat is = {rc.inv_s[q].hi, rc.inv_s[q].lo};
         const dfloat un = df_add_f(df_mul(df_add_f(df_mul(tn, d[q]), c.eye[q]), is), -0.5f);
-        r.uhi[q] = un.hi;
-        r.ulo[q] = un.lo;
         const dfloat st = df_mul(df_mul(dt, d[q]), is);
-        r.dhi[q] = st.hi;
-        r.dlo[q] = st.lo;
+        // 32.32 fixed point of the step and of sample 0's coordinate u_n + step / 2
+        r.du[q] = df_to_fx(st);
+        r.u0[q] = df_to_fx(un) + df_to_fx(dfloat{0.5f * st.hi, 0.5f * st.lo});
         r.dir[q] = d[q].hi;
     }
     return true;
 }
 
 // Cell of sample k along axis q: u_c = clamp(u, 0, n-1), i0 = min(floor(u_c), n-2),
-// f = u_c - i0. u = u_n + (k + 1/2) step is carried as a double-float (exact
-// product by FMA, exact sum by TwoSum) so that f is accurate to ~3e-8 at any
-// depth; a single-float u would carry ~1e-5 voxel, which moves steep
-// transfer-function edges by more than the 1e-4 RGBA budget. Intrinsics keep
-// the compiler from contracting the error-free transformations.
-__device__ __forceinline__ void sample_cell(const RayDev& r, int q, float kk, int n, int& i0, float& f) {
-    const float ph = __fmul_rn(kk, r.dhi[q]);
-    const float pl = fmaf(kk, r.dhi[q], -ph);
-    const float s = __fadd_rn(r.uhi[q], ph);
-    const float bb = __fsub_rn(s, r.uhi[q]);
-    const float e = __fadd_rn(__fsub_rn(r.uhi[q], __fsub_rn(s, bb)), __fsub_rn(ph, bb));
-    const float t = __fadd_rn(__fadd_rn(e, pl), fmaf(kk, r.dlo[q], r.ulo[q]));
-    const float u = __fadd_rn(s, t);
-    if (u <= 0.0f) {
+// f = u_c - i0. u = u_n + (k + 1/2) step is carried in 32.32 fixed point
+// (u0 + k du, exact integer arithmetic): the rounding of u0 and du leaves ~(k+1) 2^-33
+// voxel, ~1e-7 after thousands of samples, and the same k gives the same cell and
+// fraction in every kernel. f is the low word rounded to float once.
+__device__ __forceinline__ void sample_cell(const RayDev& r, int q, int k, int n, int& i0, float& f) {
+    const long long U = r.u0[q] + (long long)k * r.du[q];
+    if (U <= 0) {
         i0 = 0;
         f = 0.0f;
-    } else if (u >= (float)(n - 1)) {
+    } else if (U >= ((long long)(n - 1) << 32)) {
         i0 = n - 2;
         f = 1.0f;
     } else {
-        i0 = min((int)u, n - 2);
-        f = fminf(fmaxf(__fadd_rn(__fsub_rn(s, (float)i0), t), 0.0f), 1.0f);
+        i0 = (int)(U >> 32);  // <= n - 2 here
+        f = __uint2float_rn((unsigned)U) * 2.3283064365386963e-10f;  // 2^-32
     }
 }
 
@@ -231,6 +238,38 @@ __device__ __forceinline__ void derived_channels(const float4* __restrict__ bric
         }
         if (kFirst + kCount > 4) {
             const float4 m = ldg_l2_256(p + 1), t = ldg_l2_256(p + 2);
+            float* o = out + (4 - kFirst);
+            o[0] = fmaf(w, m.x, o[0]);
+            o[1] = fmaf(w, m.y, o[1]);
+            o[2] = fmaf(w, m.z, o[2]);
+            o[3] = fmaf(w, m.w, o[3]);
+            o[4] = fmaf(w, t.x, o[4]);
+            o[5] = fmaf(w, t.y, o[5]);
+        }
+    }
+}
+
+// derived_channels over a derived brick staged in shared memory (plain loads).
+template <int kFirst, int kCount>
+__device__ __forceinline__ void derived_channels_smem(const float4* brick, int E, int lx, int ly, int lz, float fx,
+                                                      float fy, float fz, float* out) {
+    const int base = (lz * E + ly) * E + lx;
+#pragma unroll
+    for (int q = 0; q < kCount; ++q) out[q] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+        const float4* p = brick + 3 * (base + (dz * E + dy) * E + dx);
+        if (kFirst == 0) {
+            const float4 a = p[0];
+            out[0] = fmaf(w, a.x, out[0]);
+            out[1] = fmaf(w, a.y, out[1]);
+            out[2] = fmaf(w, a.z, out[2]);
+            out[3] = fmaf(w, a.w, out[3]);
+        }
+        if (kFirst + kCount > 4) {
+            const float4 m = p[1], t = p[2];
             float* o = out + (4 - kFirst);
             o[0] = fmaf(w, m.x, o[0]);
             o[1] = fmaf(w, m.y, o[1]);
@@ -416,11 +455,11 @@ __device__ __forceinline__ int brick_exit_k(const RayDev& r, const int bcell[3],
     float kmin = (float)ns;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const float st = r.dhi[q];
-        if (st == 0.0f) continue;
-        const float bound = st > 0.0f ? (float)(B * (bcell[q] + 1)) : (float)(B * bcell[q]);
-        // u(k) = u_n + (k + 1/2) st crosses `bound` at k* = (bound - u_n)/st - 1/2
-        const float ks = (bound - r.uhi[q] - r.ulo[q]) / st - 0.5f;
+        const float st = fx_to_float(r.du[q]);  // step (voxels)
+        if (r.du[q] == 0) continue;
+        const int bound = st > 0.0f ? B * (bcell[q] + 1) : B * bcell[q];
+        // u(k) = (u0 + k du) 2^-32 crosses `bound` at k* = (bound 2^32 - u0) / du
+        const float ks = fx_to_float(((long long)bound << 32) - r.u0[q]) / st;
         kmin = fminf(kmin, st > 0.0f ? ceilf(ks) : floorf(ks) + 1.0f);
     }
     int ke = (int)fmaxf(kmin, 0.0f) - 1;  // back off one sample

@@ -27,7 +27,8 @@ def main():
     ap.add_argument("--workload", default="brainweb_1080p",
                     choices=["brainweb_1080p", "brainweb_540p", "head64", "diff_head128_8cam", "vessel_1080p",
                              "batched"])
-    ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil"])
+    ap.add_argument("--kernel", default="gather", choices=["gather", "staged", "stencil", "staged_derived"])
+    ap.add_argument("--brick", type=int, default=8, help="skip-brick edge in cells (4, 8 or 16)")
     ap.add_argument("--frames", type=int, default=3)
     ap.add_argument("--packet-w", type=int, default=4)
     ap.add_argument("--warps", type=int, default=4)
@@ -50,11 +51,12 @@ def main():
     else:
         case = workloads.brainweb_1080p()
     kernel = {"gather": pkg.VR_KERNEL_GATHER, "staged": pkg.VR_KERNEL_STAGED,
-              "stencil": pkg.VR_KERNEL_GATHER_STENCIL}[args.kernel]
+              "stencil": pkg.VR_KERNEL_GATHER_STENCIL, "staged_derived": pkg.VR_KERNEL_STAGED_DERIVED}[args.kernel]
     vol = case["volume"]
     data = torch.from_numpy(vol.view(np.int16) if vol.dtype == np.uint16 else vol).cuda()
     with pkg.Context(0) as ctx:
         vid = ctx.load_volume(data, case["spacing"])
+        ctx.set_brick_size(vid, args.brick)
         tp = []
         for _ in range(args.precompute_reps):
             s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -17,7 +17,8 @@ VR_OK, VR_ERR_INVALID_ARG, VR_ERR_NOT_READY, VR_ERR_CUDA, VR_ERR_OOM, VR_ERR_TIM
     range(8)
 VR_F32, VR_U16 = 0, 1
 VR_TF_1D, VR_TF_2D_GRAD, VR_TF_2D_VESSEL = 0, 1, 2
-VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL = 0, 1, 2, 3
+VR_KERNEL_AUTO, VR_KERNEL_GATHER, VR_KERNEL_STAGED, VR_KERNEL_GATHER_STENCIL, VR_KERNEL_STAGED_DERIVED = \
+    0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "VR_OK", 1: "VR_ERR_INVALID_ARG", 2: "VR_ERR_NOT_READY", 3: "VR_ERR_CUDA", 4: "VR_ERR_OOM",
                 5: "VR_ERR_TIMEOUT", 6: "VR_ERR_DEGENERATE", 7: "VR_ERR_BOUNDS"}

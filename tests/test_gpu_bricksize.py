@@ -198,3 +198,19 @@ def test_tile_shapes_render_the_same_image(vr, torch, packet_w, warps):
     np.testing.assert_array_equal(img, ref)
     np.testing.assert_array_equal(ri, rr)
     vr.free_volume(vid)
+
+
+@pytest.mark.parametrize("B,packet_w,warps", [(4, 4, 8), (4, 8, 4), (8, 4, 4), (8, 16, 2), (4, 32, 2)])
+@pytest.mark.parametrize("which", ["brainweb_2d", "head_1d"])
+def test_staged_derived_equals_gather_bitwise(vr, torch, B, packet_w, warps, which):
+    """Staging the derived bricks in shared memory changes only where the corners are
+    read from: images and per-ray sample counts equal the gather kernel's bit for bit."""
+    import paper_2605_19737_gb300 as pkg
+    case = _cases()[which]
+    vid = _load(vr, torch, case, B)
+    ref, rr = _render(vr, torch, vid, case, kernel=pkg.VR_KERNEL_GATHER)
+    img, ri = _render(vr, torch, vid, case, kernel=pkg.VR_KERNEL_STAGED_DERIVED, packet_w=packet_w,
+                      warps_per_block=warps)
+    np.testing.assert_array_equal(img, ref)
+    np.testing.assert_array_equal(ri, rr)
+    vr.free_volume(vid)
