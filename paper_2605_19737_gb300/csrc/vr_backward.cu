@@ -69,12 +69,17 @@ __device__ __forceinline__ void eval_field(const VolumeDev& v, const TissueDev& 
 // gradients of the cell's 8 corners -- up to three vector reductions per corner,
 // the Hessian ones only when the sample has Hessian gradients (a curvature term):
 // without one that removes two thirds of the reduction traffic (8-view 512^2
-// backward 36 -> 27 ms). Corners in offset order: parity order, which helps the
-// loads, measured slower here (1080p 14.1 -> 15.1 ms).
+// backward 36 -> 27 ms).
 // Per-voxel channel gradients in three planes: (I, gx, gy, gz) float4 [nvox],
 // (Hxx, Hyy, Hzz, Hxy) float4 [nvox], (Hxz, Hyz) float2 [nvox]. Every vector
 // reduction then covers one aligned 16- or 8-byte piece, and x-neighbouring voxels'
 // pieces share sectors (1080p backward 16.2 -> 14.1 ms against 48-byte records).
+// Corner order: a warp's reduction to one address is applied one lane at a time
+// (one L1 wavefront per lane: 32 lanes on one address cost 32 wavefronts, on 32
+// consecutive addresses one), and the lanes of a warp that scatter in the same
+// step are often in the same cell. Each lane therefore starts at the corner given
+// by its rank among the lanes in its cell, so that up to 8 of them hit 8 different
+// voxels in each reduction instruction. The rank only orders the additions.
 // Float index of voxel p's channel ch (0..9).
 __device__ __forceinline__ long long chan_index(long long p, long long nvox, int ch) {
     return ch < 4 ? 4 * p + ch : (ch < 8 ? 4 * nvox + 4 * p + (ch - 4) : 8 * nvox + 2 * p + (ch - 8));
@@ -89,12 +94,19 @@ __device__ __forceinline__ void scatter_channels(float* __restrict__ dgrad, cons
 #pragma unroll
     for (int q = 4; q < 10; ++q) hess |= dfs[q] != 0.0f;
     if (!any && !hess) return;
+    const long long nxy = (long long)n[0] * n[1];
+    const long long p0 = (long long)i0[2] * nxy + (long long)i0[1] * n[0] + i0[0];
+    // the lanes converged here, grouped by cell (low 32 bits of its index: a
+    // collision only merges two groups' ranks)
+    const unsigned same = __match_any_sync(__activemask(), (unsigned)p0);
+    const int rot = __popc(same & ((1u << (threadIdx.x & 31)) - 1u));
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+    for (int i = 0; i < 8; ++i) {
+        const int c = (i + rot) & 7;
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
         const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
         if (w == 0.0f) continue;
-        const long long p = ((long long)(i0[2] + dz) * n[1] + (i0[1] + dy)) * n[0] + (i0[0] + dx);
+        const long long p = p0 + dx + (dy ? (long long)n[0] : 0ll) + (dz ? nxy : 0ll);
         atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 0)),
                   make_float4(w * dfs[0], w * dfs[1], w * dfs[2], w * dfs[3]));
         if (hess) {

@@ -3,7 +3,8 @@ central finite differences of the GPU forward renderer, plus the autograd
 binding and a short transfer-function fit.
 
 Bars: normwise relative error <= 1e-3 per parameter group against the
-oracle; rays whose stopping sample is ambiguous, or that pass within float32
+oracle (at full size, a uniform's error relative to the sum of its blocks' absolute
+gradients, the scale of a float32 sum's rounding bound); rays whose stopping sample is ambiguous, or that pass within float32
 rounding of a point where the sample's opacity or colour has a kink (a
 transfer-function knot, a clamp; oracle FLAG_KINK), carry no upstream gradient
 -- there the two one-sided derivatives are both correct -- and they are at most
@@ -312,9 +313,26 @@ def test_backward_full_size_sampled(vr, torch, name):
     dtf, dpar, dvol = vr.render_backward(vid, case["cams"], W, H, torch.from_numpy(dl).cuda(), ray_state=state)
     dtf, dpar, dvol = dtf.cpu().numpy(), dpar.cpu().numpy(), dvol.cpu().numpy()
     used = [0, 1, 2, 3, 4] if case["params"]["shading"] else [0, 4]  # d/dgamma also at gamma = 0
-    e_par = max(abs(dpar[k] - dpar_o[k]) / max(abs(dpar_o[k]), 1e-6 * np.abs(dpar_o).max()) for k in used)
+    # Each uniform's gradient is a sum over thousands of rays whose signs follow the random
+    # upstream gradient; a float32 sum's rounding error is bounded relative to the sum of
+    # the terms' magnitudes (|fl(sum x) - sum x| <= gamma_n sum |x|), not to the possibly
+    # cancelling total (opacity_scale here: total 0.028 from row sums up to 2.6). The bar
+    # is taken against sum |partial gradient| over 16 blocks of rays -- a lower bound of
+    # sum |x|, so never looser than that bound -- from the oracle.
+    rows = [(c, y) for c in range(n) for y in range(0, H, 16)]
+    scale = np.zeros(5)
+    for blk in np.array_split(np.arange(len(rows)), 16):
+        d1 = np.zeros_like(dl)
+        for r in blk:
+            d1[rows[r]] = dl[rows[r]]
+        _, pb, _ = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H,
+                                      d1.astype(np.float64), gmax_value=gmax, want_volume=False)
+        scale += np.abs(pb)
+    assert np.all(scale >= np.abs(dpar_o) * (1 - 1e-12))
+    e_par = max(abs(dpar[k] - dpar_o[k]) / max(scale[k], 1e-30) for k in used)
     e_tf, e_vol = _rel(dtf, dtf_o), _rel(dvol, dvol_o)
-    print("%s full size, sampled rays: rel err tf %.2e params %.2e volume %.2e" % (name, e_tf, e_par, e_vol))
+    print("%s full size, sampled rays: rel err tf %.2e params %.2e (of sum |block|) volume %.2e" %
+          (name, e_tf, e_par, e_vol))
     assert np.linalg.norm(dtf_o) > 0 and np.linalg.norm(dvol_o) > 0
     assert e_tf <= TOL_GRAD and e_par <= TOL_GRAD and e_vol <= TOL_GRAD
     vr.free_volume(vid)
