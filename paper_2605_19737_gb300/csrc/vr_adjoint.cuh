@@ -18,32 +18,44 @@ struct ParamGrad {
 };
 
 // Transfer-function gradient sink: one of the private global copies of the
-// gradient table, one 16-byte vector reduction per RGBA entry. (Shared-memory
-// tables with scalar atomics measured 1.6x slower on a 1D table: the lanes of a
-// CTA contend for the same few entries.) A lane's consecutive samples mostly look
-// up the same transfer-function cell, so the sink accumulates the cell's (2 or 4)
-// entry gradients in registers and writes them out only when the cell changes
-// (and once at the end of the ray: flush()).
+// gradient, kept per lookup cell rather than per entry. A lane's consecutive
+// samples mostly look up the same transfer-function cell, so the sink accumulates
+// the cell's (2 or 4) entry gradients in registers and writes them out only when
+// the cell changes (and once at the end of the ray: flush()). A copy holds one
+// 16-float record per cell key (k * tf_w + j, the index of its entry (j, k)): the
+// opacity gradients of its four corner entries 00, 01, 10, 11, then their RGB
+// gradients (3 x 4 floats), written with up to four 16-byte vector reductions, all
+// zero pieces skipped; in a 1D table (two corners) the opacities of 00 and 01, then
+// the RGB of 00 and of 01 (two pieces). Samples whose opacity entry is zero (most
+// of a ray: the sweep does not skip empty space) give gradient to the opacity
+// entries only, so most flushes write one 16-byte piece where an entry-major table
+// took four (two).
+// k_sum_copies gathers each entry's share from the (up to 4) cells around it.
+// (Shared-memory tables with scalar atomics measured 1.6x slower on a 1D table:
+// the lanes of a CTA contend for the same few entries.)
+
 struct TfGradSink {
-    float* p;
-    int w;          // entries per row
+    float* p;       // this copy: [cell key][kTfCellFloats]
     bool two_d;
-    int key = -1;   // first entry of the pending cell, -1 = none
+    int key = -1;   // the pending cell, -1 = none
     float4 a00, a01, a10, a11;
 
-    __device__ __forceinline__ TfGradSink(float* p_, int w_, bool two_d_) : p(p_), w(w_), two_d(two_d_) {}
+    __device__ __forceinline__ TfGradSink(float* p_, bool two_d_) : p(p_), two_d(two_d_) {}
 
-    __device__ __forceinline__ void put(int entry, const float4& v) const {
+    __device__ __forceinline__ void put(int piece, const float4& v) const {
         if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f)
-            atomicAdd(reinterpret_cast<float4*>(p) + entry, v);
+            atomicAdd(reinterpret_cast<float4*>(p + (size_t)key * kTfCellFloats) + piece, v);
     }
     __device__ __forceinline__ void flush() {
         if (key < 0) return;
-        put(key, a00);
-        put(key + 1, a01);
         if (two_d) {
-            put(key + w, a10);
-            put(key + w + 1, a11);
+            put(0, make_float4(a00.w, a01.w, a10.w, a11.w));
+            put(1, make_float4(a00.x, a00.y, a00.z, a01.x));
+            put(2, make_float4(a01.y, a01.z, a10.x, a10.y));
+            put(3, make_float4(a10.z, a11.x, a11.y, a11.z));
+        } else {
+            put(0, make_float4(a00.w, a01.w, a00.x, a00.y));
+            put(1, make_float4(a00.z, a01.x, a01.y, a01.z));
         }
         key = -1;
     }

@@ -954,11 +954,12 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     B.dparams = d_dparams;
     B.dvol = d_dvolume;
     {
-        // private copies of the transfer-function gradient, summed after the kernels
-        // as many copies as fit 64 MB, 64 to 1024: the fewer the table's entries, the
-        // more CTAs contend for each, and the cheaper a copy is
-        const size_t tbytes = sizeof(float) * ntf;
-        const int ncopies = (int)std::min<size_t>(1024, std::max<size_t>(64, ((size_t)64 << 20) / tbytes));
+        // private copies of the transfer-function gradient (a 16-float record per
+        // lookup cell), summed after the kernels: as many copies as fit 256 MB, 8 to
+        // 1024: the fewer the table's entries, the more CTAs contend for each, and the
+        // cheaper a copy is (a 256x64 table: 256 copies of 1 MB)
+        const size_t tbytes = sizeof(float) * kTfCellFloats * (size_t)v->tp.tf_w * v->tp.tf_h;
+        const int ncopies = (int)std::min<size_t>(1024, std::max<size_t>(8, ((size_t)256 << 20) / tbytes));
         const size_t need = tbytes * ncopies;
         if (ctx->tfgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
@@ -985,7 +986,7 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     if (channels)
         CK(launch_channels_to_voxels(ctx->d_dgrad, v->n, v->s, d_dvolume, ctx->stream),
            "render_backward: channel gradients to voxels");
-    CK(launch_sum_copies(ctx->d_tfgrad, B.n_copies, (long long)ntf, d_dtf, ctx->stream),
+    CK(launch_sum_copies(ctx->d_tfgrad, B.n_copies, v->tp.tf_w, v->tp.tf_h, d_dtf, ctx->stream),
        "render_backward: sum gradient copies");
     return VR_OK;
 }

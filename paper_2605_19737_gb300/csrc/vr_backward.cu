@@ -199,11 +199,11 @@ __global__ void __launch_bounds__(256) k_channels_to_voxels(const float* __restr
 template <bool kDerived, bool kLazyHessian, bool kNoHessian, int kBS>
 __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constant__ BackwardLaunch B) {
     const RenderLaunch& L = B.r;
-    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
-    // one of n_copies private global copies of the gradient table, so that CTAs
-    // working on the same hot entries do not serialise on one address
+    const size_t ncell = (size_t)L.tp.tf_w * L.tp.tf_h * kTfCellFloats;
+    // one of n_copies private global copies of the gradient, so that CTAs working on
+    // the same hot entries do not serialise on one address
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ntf, L.tp.tf_w, L.tp.tf_h > 1);
+    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ncell, L.tp.tf_h > 1);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
     tile_pixel(L.packet_w, __ffs(tile_packets_x(L.packet_w, 4)) - 1, w, l, di, dj);
@@ -405,13 +405,13 @@ __device__ __forceinline__ unsigned far_key(const int b[3], const int e[3]) {
 __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_constant__ BackwardLaunch B) {
     extern __shared__ float smem[];
     const RenderLaunch& L = B.r;
-    const int ntf = L.tp.tf_w * L.tp.tf_h * 4;
+    const size_t ncell = (size_t)L.tp.tf_w * L.tp.tf_h * kTfCellFloats;
     const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
     float* acc = smem + warp * kBrickVox;  // this warp's 12^3 block
     for (int e = l; e < kBrickVox; e += 32) acc[e] = 0.0f;
     __syncthreads();
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ntf, L.tp.tf_w, L.tp.tf_h > 1);
+    TfGradSink sink(B.dtf_copies + (size_t)(cta % B.n_copies) * ncell, L.tp.tf_h > 1);
     const int i = blockIdx.x * 16 + (warp & 1) * 8 + (l & 7);
     const int j = blockIdx.y * 8 + (warp >> 1) * 4 + (l >> 3);
     const int cam = blockIdx.z;
@@ -592,19 +592,35 @@ __global__ void __launch_bounds__(128) k_render_backward_staged(const __grid_con
     }
 }
 
-// dtf[e] += the sum of copies [16 g, 16 g + 16) of entry e, one thread per (e, g):
-// enough threads for a small table with many copies (dtf is zeroed before).
+// dtf[e] += the sum over copies [16 g, 16 g + 16) of entry e's share of the cells
+// around it, one thread per (float e, g): enough threads for a small table with many
+// copies (dtf is zeroed before). Entry (j, k) is corner 00 of cell (j, k), 01 of
+// (j - 1, k), 10 of (j, k - 1) and 11 of (j - 1, k - 1), where those cells exist (a
+// cell's j < w - 1 and, in a 2D table, k < h - 1); in a cell record the opacity of
+// corner q is float q, its RGB floats 4 + 3 q .. 6 + 3 q (1D: 2 + 3 q .. 4 + 3 q).
 constexpr int kCopiesPerThread = 16;
-__global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ copies, int n_copies, long long n,
+__global__ void __launch_bounds__(256) k_sum_copies(const float* __restrict__ copies, int n_copies, int w, int h,
                                                    float* __restrict__ out) {
+    const long long n = 4ll * w * h;
+    const long long stride = (long long)w * h * kTfCellFloats;
     const long long groups = (n_copies + kCopiesPerThread - 1) / kCopiesPerThread;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n * groups;
          t += (long long)gridDim.x * blockDim.x) {
         const long long e = t % n;
+        const int ch = (int)(e & 3), entry = (int)(e >> 2), j = entry % w, k = entry / w;
         const int c0 = (int)(t / n) * kCopiesPerThread;
         const int c1 = min(c0 + kCopiesPerThread, n_copies);
+        // (cell key, float in its record) of each corner this entry is
+        int off[4], m = 0;
+        const bool kin = h == 1 || k < h - 1;  // row k holds cells
+        auto slot = [&](int q) { return ch == 3 ? q : (h > 1 ? 4 : 2) + 3 * q + ch; };
+        if (j < w - 1 && kin) off[m++] = entry * kTfCellFloats + slot(0);
+        if (j >= 1 && kin) off[m++] = (entry - 1) * kTfCellFloats + slot(1);
+        if (h > 1 && k >= 1 && j < w - 1) off[m++] = (entry - w) * kTfCellFloats + slot(2);
+        if (h > 1 && k >= 1 && j >= 1) off[m++] = (long long)(entry - w - 1) * kTfCellFloats + slot(3);
         float acc = 0.0f;
-        for (int c = c0; c < c1; ++c) acc += __ldg(copies + (size_t)c * n + e);
+        for (int c = c0; c < c1; ++c)
+            for (int u = 0; u < m; ++u) acc += __ldg(copies + (size_t)c * stride + off[u]);
         if (acc != 0.0f) atomicAdd(out + e, acc);
     }
 }
@@ -620,9 +636,11 @@ cudaError_t launch_channels_to_voxels(const float* dgrad, const int n[3], const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st) {
+cudaError_t launch_sum_copies(const float* copies, int n_copies, int tf_w, int tf_h, float* dtf, cudaStream_t st) {
+    const long long n = 4ll * tf_w * tf_h;
     const long long blocks = (n * ((n_copies + kCopiesPerThread - 1) / kCopiesPerThread) + 255) / 256;
-    k_sum_copies<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(copies, n_copies, n, dtf);
+    k_sum_copies<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256, 0, st>>>(copies, n_copies, tf_w, tf_h,
+                                                                               dtf);
     return cudaGetLastError();
 }
 

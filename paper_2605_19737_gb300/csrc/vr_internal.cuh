@@ -153,13 +153,17 @@ __device__ __forceinline__ void tile_pixel(int packet_w, int sx, int w, int l, i
     dj = wy * (32 >> pl) + (l >> pl);
 }
 
+// floats per lookup cell in a private copy of the transfer-function gradient
+constexpr int kTfCellFloats = 16;
+
 struct BackwardLaunch {
     RenderLaunch r;
     const float* dl_drgba;  // [n_cams][H][W][4] upstream gradient
     float* dtf;             // [tf_h][tf_w][4], zeroed by the caller
     float* dparams;         // gamma, ka, kd, ks, opacity_scale, zeroed by the caller
     float* dvol;            // nvox or nullptr, zeroed by the caller
-    float* dtf_copies;      // n_copies zeroed private copies of dtf (CTA c adds into copy c % n_copies)
+    float* dtf_copies;      // n_copies zeroed private copies of the transfer-function gradient, one
+                            // 16-float record per lookup cell (TfGradSink); CTA c adds into copy c % n_copies
     int n_copies;
     float* dgrad;           // derived-brick path with dvol: zeroed channel gradients (10 floats per voxel
                             // in three planes, chan_index), else nullptr
@@ -230,8 +234,8 @@ cudaError_t launch_gauss3d(const float* in, float* out, float* tmp, const int n[
 // warps: warps per CTA (2, 4 or 8), tiled by tile_pixel.
 cudaError_t launch_render_gather(const RenderLaunch& L, int warps, cudaStream_t st);
 cudaError_t launch_render_backward(const BackwardLaunch& B, bool staged, cudaStream_t st);
-// dtf[e] = sum over c of copies[c * n + e]
-cudaError_t launch_sum_copies(const float* copies, int n_copies, long long n, float* dtf, cudaStream_t st);
+// dtf += the entries' shares of the cell records of every copy
+cudaError_t launch_sum_copies(const float* copies, int n_copies, int tf_w, int tf_h, float* dtf, cudaStream_t st);
 cudaError_t launch_fma_peak(float* out, int blocks, int iters, cudaStream_t st);
 cudaError_t launch_wait_probe(unsigned* status, long long budget_cycles, cudaStream_t st);
 // One thread fails one index check (debug builds record it; release builds do nothing).
