@@ -67,10 +67,8 @@ struct TfGradSink {
             a00 = a01 = a10 = a11 = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         auto acc = [&](float4& a, float c) {
-            a.x = fmaf(c, d[0], a.x);
-            a.y = fmaf(c, d[1], a.y);
-            a.z = fmaf(c, d[2], a.z);
-            a.w = fmaf(c, d[3], a.w);
+            fma2(c, d[0], d[1], a.x, a.y);
+            fma2(c, d[2], d[3], a.z, a.w);
         };
         acc(a00, w00);
         acc(a01, w01);

@@ -107,12 +107,18 @@ __device__ __forceinline__ void scatter_channels(float* __restrict__ dgrad, cons
         const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
         if (w == 0.0f) continue;
         const long long p = p0 + dx + (dy ? (long long)n[0] : 0ll) + (dz ? nxy : 0ll);
-        atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 0)),
-                  make_float4(w * dfs[0], w * dfs[1], w * dfs[2], w * dfs[3]));
+        float4 g0;
+        mul2(w, w, dfs[0], dfs[1], g0.x, g0.y);
+        mul2(w, w, dfs[2], dfs[3], g0.z, g0.w);
+        atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 0)), g0);
         if (hess) {
-            atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 4)),
-                      make_float4(w * dfs[4], w * dfs[5], w * dfs[6], w * dfs[7]));
-            atomicAdd(reinterpret_cast<float2*>(dgrad + chan_index(p, nvox, 8)), make_float2(w * dfs[8], w * dfs[9]));
+            float4 g1;
+            float2 g2;
+            mul2(w, w, dfs[4], dfs[5], g1.x, g1.y);
+            mul2(w, w, dfs[6], dfs[7], g1.z, g1.w);
+            mul2(w, w, dfs[8], dfs[9], g2.x, g2.y);
+            atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 4)), g1);
+            atomicAdd(reinterpret_cast<float2*>(dgrad + chan_index(p, nvox, 8)), g2);
         }
     }
 }

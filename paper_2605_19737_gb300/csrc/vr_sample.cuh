@@ -215,11 +215,51 @@ __device__ __forceinline__ float4 ldg_l2_256(const float4* p) {
     return v;
 }
 
+// (ox, oy) = (fma(w, ax, ox), fma(w, ay, oy)) in one packed instruction
+// (fma.rn.f32x2, sm_100 and later): each half rounds exactly as fmaf does, so the
+// results are bit-identical to two scalar FMAs in half the issue slots.
+__device__ __forceinline__ void fma2(float w, float ax, float ay, float& ox, float& oy) {
+    asm("{\n\t.reg .b64 pw, pa, po;\n\t"
+        "mov.b64 pw, {%2, %2};\n\t"
+        "mov.b64 pa, {%3, %4};\n\t"
+        "mov.b64 po, {%0, %1};\n\t"
+        "fma.rn.f32x2 po, pw, pa, po;\n\t"
+        "mov.b64 {%0, %1}, po;\n\t}"
+        : "+f"(ox), "+f"(oy)
+        : "f"(w), "f"(ax), "f"(ay));
+}
+
+// (ox, oy) = (ax * bx, ay * by) in one packed instruction (mul.rn.f32x2).
+__device__ __forceinline__ void mul2(float ax, float ay, float bx, float by, float& ox, float& oy) {
+    asm("{\n\t.reg .b64 pa, pb;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pa, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pa;\n\t}"
+        : "=f"(ox), "=f"(oy)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+
+// Trilinear weights of the 8 corners in offset order c = dx + 2 dy + 4 dz,
+// ((dx ? fx : 1 - fx) * (dy ? fy : 1 - fy)) * (dz ? fz : 1 - fz), the x pairs in packed
+// multiplies (the same products, rounded the same way).
+__device__ __forceinline__ void corner_weights(float fx, float fy, float fz, float w[8]) {
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+#pragma unroll
+    for (int yz = 0; yz < 4; ++yz) {
+        const float wy = (yz & 1) ? fy : gy, wz = (yz & 2) ? fz : gz;
+        mul2(gx, fx, wy, wy, w[2 * yz], w[2 * yz + 1]);
+        mul2(w[2 * yz], w[2 * yz + 1], wz, wz, w[2 * yz], w[2 * yz + 1]);
+    }
+}
+
 template <bool kParity, int kFirst, int kCount>
 __device__ __forceinline__ void derived_channels(const float4* __restrict__ brick, int E, int lx, int ly, int lz,
                                                  float fx, float fy, float fz, float* out) {
     const int px = kParity ? lx & 1 : 0, py = kParity ? ly & 1 : 0, pz = kParity ? lz & 1 : 0;
     const int base = (lz * E + ly) * E + lx;
+    float wo[8];
+    if (!kParity) corner_weights(fx, fy, fz, wo);
 #pragma unroll
     for (int q = 0; q < kCount; ++q) out[q] = 0.0f;
 #pragma unroll
@@ -227,24 +267,20 @@ __device__ __forceinline__ void derived_channels(const float4* __restrict__ bric
         // kParity: the corner of parity (c & 1, c >> 1 & 1, c >> 2 & 1), i.e. offset
         // parity ^ cell parity; otherwise the corner at offset (c & 1, c >> 1 & 1, c >> 2 & 1)
         const int dx = px ^ (c & 1), dy = py ^ ((c >> 1) & 1), dz = pz ^ ((c >> 2) & 1);
-        const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+        const float w =
+            kParity ? (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz) : wo[c];
         const float4* p = brick + 3 * (base + (dz * E + dy) * E + dx);
         if (kFirst == 0) {
             const float4 a = ldg_l2_256(p);
-            out[0] = fmaf(w, a.x, out[0]);
-            out[1] = fmaf(w, a.y, out[1]);
-            out[2] = fmaf(w, a.z, out[2]);
-            out[3] = fmaf(w, a.w, out[3]);
+            fma2(w, a.x, a.y, out[0], out[1]);
+            fma2(w, a.z, a.w, out[2], out[3]);
         }
         if (kFirst + kCount > 4) {
             const float4 m = ldg_l2_256(p + 1), t = ldg_l2_256(p + 2);
             float* o = out + (4 - kFirst);
-            o[0] = fmaf(w, m.x, o[0]);
-            o[1] = fmaf(w, m.y, o[1]);
-            o[2] = fmaf(w, m.z, o[2]);
-            o[3] = fmaf(w, m.w, o[3]);
-            o[4] = fmaf(w, t.x, o[4]);
-            o[5] = fmaf(w, t.y, o[5]);
+            fma2(w, m.x, m.y, o[0], o[1]);
+            fma2(w, m.z, m.w, o[2], o[3]);
+            fma2(w, t.x, t.y, o[4], o[5]);
         }
     }
 }
@@ -263,20 +299,15 @@ __device__ __forceinline__ void derived_channels_smem(const float4* brick, int E
         const float4* p = brick + 3 * (base + (dz * E + dy) * E + dx);
         if (kFirst == 0) {
             const float4 a = p[0];
-            out[0] = fmaf(w, a.x, out[0]);
-            out[1] = fmaf(w, a.y, out[1]);
-            out[2] = fmaf(w, a.z, out[2]);
-            out[3] = fmaf(w, a.w, out[3]);
+            fma2(w, a.x, a.y, out[0], out[1]);
+            fma2(w, a.z, a.w, out[2], out[3]);
         }
         if (kFirst + kCount > 4) {
             const float4 m = p[1], t = p[2];
             float* o = out + (4 - kFirst);
-            o[0] = fmaf(w, m.x, o[0]);
-            o[1] = fmaf(w, m.y, o[1]);
-            o[2] = fmaf(w, m.z, o[2]);
-            o[3] = fmaf(w, m.w, o[3]);
-            o[4] = fmaf(w, t.x, o[4]);
-            o[5] = fmaf(w, t.y, o[5]);
+            fma2(w, m.x, m.y, o[0], o[1]);
+            fma2(w, m.z, m.w, o[2], o[3]);
+            fma2(w, t.x, t.y, o[4], o[5]);
         }
     }
 }
