@@ -65,17 +65,29 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     bool cur_empty = false;
     const float4* dbrick = nullptr;  // derived brick of cur_bi
     const int bs = kBS ? kBS : v.bs, B = 1 << bs, E = B + 1;
+    // the position of sample k, u0 + k du, carried by exact integer additions
+    long long U[3] = {r.u0[0], r.u0[1], r.u0[2]};
+    auto advance = [&](int k1) {
+        if (k1 == k + 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) U[q] += r.du[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) U[q] += (long long)(k1 - k) * r.du[q];
+        }
+        k = k1;
+    };
     while (k < r.ns) {
         int i0[3], bc[3];
         float f[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            sample_cell(r, q, k, v.n[q], i0[q], f[q]);
+            cell_at(U[q], v.n[q], i0[q], f[q]);
             bc[q] = i0[q] >> bs;
         }
         if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&
                                      (unsigned)bc[2] < (unsigned)v.nb[2])) {
-            ++k;
+            advance(k + 1);
             continue;
         }
         const int bi = brick_index(v, bc);
@@ -87,7 +99,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
                     v.dbricks + (size_t)bi * (kBS ? (size_t)der_brick_floats(kBS) : (size_t)v.der_stride));
         }
         if (skip && cur_empty) {
-            k = brick_exit_k(r, bc, B, k, r.ns);
+            advance(brick_exit_k_at(r, U, bc, B, k, r.ns));
             continue;
         }
         // local cell of (i0, j0, k0) within the skip brick: i0 - B bc = i0 & (B - 1)
@@ -98,7 +110,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             const int c = (((lz << bs) + ly) << bs) + lx;
             if ((__ldg(v.cellmask + (size_t)bi * cell_words(bs) + (c >> 5)) >> (c & 31)) & 1u) {
                 ++ne;
-                ++k;
+                advance(k + 1);
                 continue;
             }
         }
@@ -120,7 +132,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             optics_tf(fld, vval, tp, tf, inv_gmax, o);
             if (o.c.w == 0.0f) {
                 ++ne;
-                ++k;
+                advance(k + 1);
                 continue;
             }
             if (!kHessianFirst) load_hessian<kParity>(tp, dbrick, E, lx, ly, lz, f, fld);
@@ -153,7 +165,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             kstop = k;
             break;
         }
-        ++k;
+        advance(k + 1);
     }
     out = make_float4(C0, C1, C2, A);
     dense = kstop >= 0 ? (unsigned)(kstop + 1) : (unsigned)r.ns;

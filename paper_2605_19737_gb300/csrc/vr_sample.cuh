@@ -124,6 +124,17 @@ __device__ __forceinline__ void sample_cell(const RayDev& r, int q, int k, int n
     }
 }
 
+// sample_cell from the sample's position U = u0 + k du itself (the march carries U
+// from sample to sample by exact integer additions): the same cell and fraction,
+// the clamps taken on the high word (U <= 0 gives (0, 0) either way; U >=
+// (n - 1) 2^32 exactly when the high word is >= n - 1).
+__device__ __forceinline__ void cell_at(long long U, int n, int& i0, float& f) {
+    const int hi = (int)(U >> 32);
+    const float fl = __uint2float_rn((unsigned)U) * 2.3283064365386963e-10f;  // 2^-32
+    i0 = min(max(hi, 0), n - 2);
+    f = hi < 0 ? 0.0f : (hi > n - 2 ? 1.0f : fl);
+}
+
 // Sample field: out = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (not yet divided
 // by the spacing). `load(o)` returns the brick value at flat offset o; `base` is
 // the offset of tap (0,0,0) = voxel (i0-1, j0-1, k0-1).
@@ -482,6 +493,25 @@ __device__ __forceinline__ int storage_brick(const VolumeDev& v, const int i0[3]
 // First sample index >= k whose cell lies outside the skip brick (b0, b1, b2) of B
 // cells per edge, for a ray currently in that brick; a lower bound (one sample
 // earlier is re-tested by the caller), never beyond ns.
+// brick_exit_k from the position U[q] = u0 + k du of the current sample k: the
+// crossing counted in steps from k (a smaller, so more precise, float quotient);
+// conservative in the same way.
+__device__ __forceinline__ int brick_exit_k_at(const RayDev& r, const long long U[3], const int bcell[3], int B,
+                                               int k, int ns) {
+    float kmin = (float)(ns - k);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float st = fx_to_float(r.du[q]);
+        if (r.du[q] == 0) continue;
+        const int bound = st > 0.0f ? B * (bcell[q] + 1) : B * bcell[q];
+        const float ks = fx_to_float(((long long)bound << 32) - U[q]) / st;
+        kmin = fminf(kmin, st > 0.0f ? ceilf(ks) : floorf(ks) + 1.0f);
+    }
+    int ke = k + (int)fmaxf(kmin, 0.0f) - 1;  // back off one sample
+    if (ke <= k) ke = k + 1;
+    return min(ke, ns);
+}
+
 __device__ __forceinline__ int brick_exit_k(const RayDev& r, const int bcell[3], int B, int k, int ns) {
     float kmin = (float)ns;
 #pragma unroll
