@@ -148,8 +148,7 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
         }
         ++nsh;
         const float wgt = (1.0f - A) * alpha;  // Eqs. 5-6
-        C0 = fmaf(col[0], wgt, C0);
-        C1 = fmaf(col[1], wgt, C1);
+        fma2v(col[0], col[1], wgt, wgt, C0, C1);
         C2 = fmaf(col[2], wgt, C2);
         if (kState) {
             A_prev = A;

@@ -240,6 +240,18 @@ __device__ __forceinline__ void fma2(float w, float ax, float ay, float& ox, flo
         : "f"(w), "f"(ax), "f"(ay));
 }
 
+// (cx, cy) = (fma(ax, bx, cx), fma(ay, by, cy)) in one packed instruction.
+__device__ __forceinline__ void fma2v(float ax, float ay, float bx, float by, float& cx, float& cy) {
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(cx), "+f"(cy)
+        : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+
 // (ox, oy) = (ax * bx, ay * by) in one packed instruction (mul.rn.f32x2).
 __device__ __forceinline__ void mul2(float ax, float ay, float bx, float by, float& ox, float& oy) {
     asm("{\n\t.reg .b64 pa, pb;\n\t"
@@ -420,8 +432,13 @@ __device__ __forceinline__ void optics_rest(const float f[10], const float dir[3
     const float gx = f[1], gy = f[2], gz = f[3];
     o.kappa = o.Hgx = o.Hgy = o.Hgz = 0.0f;
     if (o.gg > 0.0f) {
-        o.Hgx = fmaf(f[4], gx, fmaf(f[7], gy, f[8] * gz));
-        o.Hgy = fmaf(f[7], gx, fmaf(f[5], gy, f[9] * gz));
+        // H g: the x and y rows in packed pairs (the same FMA chains)
+        float hgx, hgy;
+        mul2(f[8], f[9], gz, gz, hgx, hgy);
+        fma2v(f[7], f[5], gy, gy, hgx, hgy);
+        fma2v(f[4], f[7], gx, gx, hgx, hgy);
+        o.Hgx = hgx;
+        o.Hgy = hgy;
         o.Hgz = fmaf(f[8], gx, fmaf(f[9], gy, f[6] * gz));
         o.kappa = fmaf(gx, o.Hgx, fmaf(gy, o.Hgy, gz * o.Hgz)) * (o.r * o.r);
     }
@@ -439,8 +456,8 @@ __device__ __forceinline__ void optics_rest(const float f[10], const float dir[3
         const float d2 = o.d * o.d, d4 = d2 * d2, d8 = d4 * d4, d16 = d8 * d8;
         const float lit = fmaf(tp.kd, o.d, tp.ka);
         const float spec = tp.ks * d16;
-        o.col[0] = fmaf(o.c.x, lit, spec);
-        o.col[1] = fmaf(o.c.y, lit, spec);
+        o.col[0] = o.col[1] = spec;
+        fma2v(o.c.x, o.c.y, lit, lit, o.col[0], o.col[1]);
         o.col[2] = fmaf(o.c.z, lit, spec);
     } else {
         o.col[0] = o.c.x;
