@@ -340,13 +340,17 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
             // whose ray reaches that far works on its sample kr, so neighbouring rays sit
             // at nearly the same depth and their reads and reductions hit the same cells
             const int kmax = __reduce_max_sync(0xffffffffu, kstop);
-            for (int kr = kmax; kr >= 0; --kr) {
+            // the position of sample kr, u0 + kr du, carried down by exact integer steps
+            long long U[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) U[q] = hit ? r.u0[q] + (long long)kmax * r.du[q] : 0ll;
+            for (int kr = kmax; kr >= 0; --kr, U[0] -= r.du[0], U[1] -= r.du[1], U[2] -= r.du[2]) {
                 if (kr > kstop) continue;
                 int i0[3], bc[3];
                 float f[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    sample_cell(r, q, kr, v.n[q], i0[q], f[q]);
+                    cell_at(U[q], v.n[q], i0[q], f[q]);
                     bc[q] = i0[q] >> kBS;
                 }
                 // No skipping here: a sample in an empty brick has alpha = 0, but its lookup
