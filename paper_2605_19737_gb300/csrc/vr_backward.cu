@@ -141,22 +141,36 @@ __device__ __forceinline__ void scatter_channels(float* __restrict__ dgrad, cons
     }
     const bool h = hess || (merged && phess_v);
     const unsigned same = __match_any_sync(__activemask(), lo);
-    const int rot = __popc(same & ((1u << lane) - 1u));
+    const int rot = __popc(same & ((1u << lane) - 1u)) & 7;
+    // instruction i scatters corner i ^ rot: per axis the two factors and offsets
+    // are swapped once when that bit of rot is set, so that every corner's weight,
+    // ((dx ? fx : 1 - fx) * (dy ? ...)) * (dz ? ...), and address are fixed registers
+    const bool sx = rot & 1, sy = (rot >> 1) & 1, sz = (rot >> 2) & 1;
+    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+    const float ax[2] = {sx ? f[0] : gx, sx ? gx : f[0]}, ay[2] = {sy ? f[1] : gy, sy ? gy : f[1]},
+                az[2] = {sz ? f[2] : gz, sz ? gz : f[2]};
+    const float qx = 1.0f - pf[0], qy = 1.0f - pf[1], qz = 1.0f - pf[2];
+    const float bx2[2] = {sx ? pf[0] : qx, sx ? qx : pf[0]}, by2[2] = {sy ? pf[1] : qy, sy ? qy : pf[1]},
+                bz2[2] = {sz ? pf[2] : qz, sz ? qz : pf[2]};
+    const int nx = n[0], nxy32 = n[0] * n[1];  // < 2^23 for dims <= 2048
+    const int ox[2] = {sx ? 1 : 0, sx ? 0 : 1}, oy[2] = {sy ? nx : 0, sy ? 0 : nx},
+              oz[2] = {sz ? nxy32 : 0, sz ? 0 : nxy32};
+    float4* const c0 = reinterpret_cast<float4*>(dgrad + chan_index(p0, nvox, 0));
+    float4* const c1 = reinterpret_cast<float4*>(dgrad + chan_index(p0, nvox, 4));
+    float2* const c2 = reinterpret_cast<float2*>(dgrad + chan_index(p0, nvox, 8));
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        const int c = (i + rot) & 7;
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
-        const float pw =
-            merged ? (dx ? pf[0] : 1.0f - pf[0]) * (dy ? pf[1] : 1.0f - pf[1]) * (dz ? pf[2] : 1.0f - pf[2]) : 0.0f;
+        const int ix = i & 1, iy = (i >> 1) & 1, iz = i >> 2;
+        const float w = (ax[ix] * ay[iy]) * az[iz];
+        const float pw = merged ? (bx2[ix] * by2[iy]) * bz2[iz] : 0.0f;
         if (w == 0.0f && pw == 0.0f) continue;
-        const long long p = p0 + dx + (dy ? (long long)n[0] : 0ll) + (dz ? nxy : 0ll);
+        const int off = ox[ix] + oy[iy] + oz[iz];
         float4 g0;
         mul2(w, w, dfs[0], dfs[1], g0.x, g0.y);
         mul2(w, w, dfs[2], dfs[3], g0.z, g0.w);
         fma2(pw, pd[0], pd[1], g0.x, g0.y);
         fma2(pw, pd[2], pd[3], g0.z, g0.w);
-        atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 0)), g0);
+        atomicAdd(c0 + off, g0);
         if (h) {
             float4 g1;
             float2 g2;
@@ -166,8 +180,8 @@ __device__ __forceinline__ void scatter_channels(float* __restrict__ dgrad, cons
             fma2(pw, pd[4], pd[5], g1.x, g1.y);
             fma2(pw, pd[6], pd[7], g1.z, g1.w);
             fma2(pw, pd[8], pd[9], g2.x, g2.y);
-            atomicAdd(reinterpret_cast<float4*>(dgrad + chan_index(p, nvox, 4)), g1);
-            atomicAdd(reinterpret_cast<float2*>(dgrad + chan_index(p, nvox, 8)), g2);
+            atomicAdd(c1 + off, g1);
+            atomicAdd(c2 + off, g2);
         }
     }
 }
