@@ -79,10 +79,9 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
     };
     while (k < r.ns) {
         int i0[3], bc[3];
-        float f[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            cell_at(U[q], v.n[q], i0[q], f[q]);
+            i0[q] = cell_index_at(U[q], v.n[q]);
             bc[q] = i0[q] >> bs;
         }
         if (!VR_CHECK(tp.status, (unsigned)bc[0] < (unsigned)v.nb[0] && (unsigned)bc[1] < (unsigned)v.nb[1] &&
@@ -115,6 +114,10 @@ __device__ __forceinline__ void march_gather(const VolumeDev& v, const TissueDev
             }
         }
         ++nip;
+        // the sample's fractions, only for samples that are evaluated
+        float f[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f[q] = cell_frac_at(U[q], v.n[q]);
         int base = 0, sbi = 0;
         if (!kDerived || v.vbricks) sbi = storage_brick(v, i0, base);
         const float vval =

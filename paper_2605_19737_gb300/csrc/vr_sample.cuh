@@ -128,11 +128,15 @@ __device__ __forceinline__ void sample_cell(const RayDev& r, int q, int k, int n
 // from sample to sample by exact integer additions): the same cell and fraction,
 // the clamps taken on the high word (U <= 0 gives (0, 0) either way; U >=
 // (n - 1) 2^32 exactly when the high word is >= n - 1).
-__device__ __forceinline__ void cell_at(long long U, int n, int& i0, float& f) {
+__device__ __forceinline__ int cell_index_at(long long U, int n) { return min(max((int)(U >> 32), 0), n - 2); }
+__device__ __forceinline__ float cell_frac_at(long long U, int n) {
     const int hi = (int)(U >> 32);
     const float fl = __uint2float_rn((unsigned)U) * 2.3283064365386963e-10f;  // 2^-32
-    i0 = min(max(hi, 0), n - 2);
-    f = hi < 0 ? 0.0f : (hi > n - 2 ? 1.0f : fl);
+    return hi < 0 ? 0.0f : (hi > n - 2 ? 1.0f : fl);
+}
+__device__ __forceinline__ void cell_at(long long U, int n, int& i0, float& f) {
+    i0 = cell_index_at(U, n);
+    f = cell_frac_at(U, n);
 }
 
 // Sample field: out = I, gx, gy, gz, Hxx, Hyy, Hzz, Hxy, Hxz, Hyz (not yet divided
