@@ -313,7 +313,10 @@ vr_status vr_reduce_minmax(vr_ctx* ctx, const void* d_data, vr_dtype dtype, long
  * Eqs. 5-6, early termination, and empty-space skipping.
  *   h_cams: n_cams cameras in host memory (copied at launch).
  *   out_rgba: n_cams*H*W*4 float32 -- device memory, or host memory when
- *             out_on_host (then the image is copied back on the stream).
+ *             out_on_host: page-locked (pinned) host memory is written by the
+ *             kernel itself through its device mapping, other host memory through
+ *             a device staging buffer and a copy back on the stream. Either way
+ *             the image is complete after the next vr_synchronize.
  *   opts: NULL for defaults (fastest kernel, skipping on).
  *   d_counters: NULL or device vr_counters to add into.
  *   d_ray_samples: NULL or device uint32 [n_cams][H][W][2] receiving each

@@ -837,9 +837,21 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
     DeviceGuard g(ctx->device);
     float* dst = out_rgba;
     const size_t img_bytes = sizeof(float) * 4 * (size_t)n_cams * W * H;
+    bool copy_back = false;
     if (out_on_host) {
-        CK(ensure_stage(ctx, img_bytes), "render: image staging buffer");
-        dst = (float*)ctx->d_stage;
+        // page-locked host memory is mapped into the device's address space: the kernel
+        // writes the image there itself, over the host link, while it renders; other
+        // host memory goes through a device staging buffer and a copy on the stream
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out_rgba) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            dst = static_cast<float*>(pa.devicePointer);
+        } else {
+            (void)cudaGetLastError();  // an unregistered pointer is not an error here
+            CK(ensure_stage(ctx, img_bytes), "render: image staging buffer");
+            dst = (float*)ctx->d_stage;
+            copy_back = true;
+        }
     }
     RenderLaunch L;
     fill_launch(L, v, W, H, o.skip_empty);
@@ -891,7 +903,7 @@ vr_status vr_render(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, int n_cams
             CK(launch_render_gather(L, o.warps_per_block, ctx->stream), "render kernel");
         }
     }
-    if (out_on_host)
+    if (copy_back)
         CK(cudaMemcpyAsync(out_rgba, dst, img_bytes, cudaMemcpyDeviceToHost, ctx->stream), "render: copy image back");
     return VR_OK;
 }

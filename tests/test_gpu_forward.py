@@ -244,10 +244,16 @@ def test_zero_opacity_and_host_output(vr, torch):
     case = workloads.head64_128px()
     vid = _load_case(vr, torch, case)
     dev = vr.render(vid, case["cams"], 128, 128)
+    # pinned host memory: written by the kernel through its device mapping
     host = torch.empty((1, 128, 128, 4), dtype=torch.float32).pin_memory()
     vr.render(vid, case["cams"], 128, 128, out=host)
     vr.synchronize()
     np.testing.assert_array_equal(dev.cpu().numpy(), host.numpy())
+    # pageable host memory: through the staging buffer and a copy back
+    pageable = torch.full((1, 128, 128, 4), -1.0, dtype=torch.float32)
+    vr.render(vid, case["cams"], 128, 128, out=pageable)
+    vr.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), pageable.numpy())
     vr.set_tissue_params(vid, ph.tf_constant((1, 1, 1), 0.0), **case["params"])
     z = vr.render(vid, case["cams"], 128, 128)
     assert float(z.abs().max()) == 0.0
