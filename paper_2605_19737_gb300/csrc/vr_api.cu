@@ -967,11 +967,12 @@ vr_status vr_render_backward(vr_ctx* ctx, int vol_id, const vr_camera* h_cams, i
     B.dvol = d_dvolume;
     {
         // private copies of the transfer-function gradient (a 16-float record per
-        // lookup cell), summed after the kernels: as many copies as fit 256 MB, 8 to
-        // 1024: the fewer the table's entries, the more CTAs contend for each, and the
-        // cheaper a copy is (a 256x64 table: 256 copies of 1 MB)
+        // lookup cell), summed after the kernels: as many copies as fit 64 MB (so that
+        // they stay in L2; 256 MB measured 1 % slower), 8 to 1024: the fewer the table's
+        // entries, the more CTAs contend for each, and the cheaper a copy is (a 256x64
+        // table: 64 copies of 1 MB)
         const size_t tbytes = sizeof(float) * kTfCellFloats * (size_t)v->tp.tf_w * v->tp.tf_h;
-        const int ncopies = (int)std::min<size_t>(1024, std::max<size_t>(8, ((size_t)256 << 20) / tbytes));
+        const int ncopies = (int)std::min<size_t>(1024, std::max<size_t>(8, ((size_t)64 << 20) / tbytes));
         const size_t need = tbytes * ncopies;
         if (ctx->tfgrad_cap < need) {
             CK(cudaStreamSynchronize(ctx->stream), "render_backward: scratch sync");
