@@ -103,6 +103,42 @@ def test_backward_matches_oracle_gradient(vr, torch, name, kernel):
     vr.free_volume(vid)
 
 
+@pytest.mark.parametrize("packet_w", [4, 8, 16])
+def test_merged_scatter_at_dense_rays(vr, torch, packet_w):
+    """Rays ~0.25 voxel apart, so that neighbouring lanes of a packet sample the same
+    cell at the same step and the backward merges their channel-gradient scatter
+    (horizontal pairs, then vertical pairs lane ^ packet_w), with a curvature term
+    (Hessian channel gradients) and every packet shape: the gradients still match the
+    oracle's."""
+    base = _cases()["head_1d"]
+    dims = (28, 26, 24)
+    case = dict(base, W=96, H=88, cams=ph.camera_array([ph.orbit_camera(dims, (1, 1, 1), 35, 15, width=96,
+                                                                         height=88, fov_deg=14.0)]))
+    In32 = oracle.normalize(case["volume"]).astype(np.float32)
+    In = In32.astype(np.float64)
+    vid = _setup(vr, torch, case, In32)
+    _, _, gmax = vr.get_norm(vid)
+    n, H, W = 1, case["H"], case["W"]
+    dl = np.random.default_rng(79).normal(size=(n, H, W, 4))
+    P = oracle_params(case["params"], case["tf"])
+    fwd = oracle.render(In, case["spacing"], P, case["tf"], case["cams"], W, H, gmax_value=gmax, alternatives=False)
+    amb = (fwd.flags & (oracle.FLAG_ET | oracle.FLAG_COUNT | oracle.FLAG_KINK)) != 0
+    assert amb.mean() <= 0.05
+    dl[amb] = 0.0
+    dtf_o, dpar_o, dvol_o = oracle.render_grad(In, case["spacing"], P, case["tf"], case["cams"], W, H, dl,
+                                               gmax_value=gmax)
+    state = torch.empty((n, H, W, 2), dtype=torch.float32, device="cuda")
+    vr.render(vid, case["cams"], W, H, ray_state=state)
+    dtf, dpar, dvol = vr.render_backward(vid, case["cams"], W, H, torch.from_numpy(dl.astype(np.float32)).cuda(),
+                                         ray_state=state, packet_w=packet_w)
+    dtf, dvol = dtf.cpu().numpy(), dvol.cpu().numpy()
+    e_tf, e_vol = _rel(dtf, dtf_o), _rel(dvol, dvol_o)
+    print("packet %d: rel err tf %.2e volume %.2e" % (packet_w, e_tf, e_vol))
+    assert np.linalg.norm(dvol_o) > 0
+    assert e_tf <= TOL_GRAD and e_vol <= TOL_GRAD
+    vr.free_volume(vid)
+
+
 @pytest.mark.parametrize("variant", ["et", "no_et", "opaque_no_et"])
 def test_ray_state_replaces_the_re_march(vr, torch, variant):
     """The per-ray state the forward records (last sample, transmittance in front of
