@@ -401,7 +401,9 @@ __global__ void __launch_bounds__(128, 4) k_render_backward(const __grid_constan
                     optics_core(fld, vval, r.dir, L.tp, tf, inv_gmax, so);
                 }
                 const float alpha = so.alpha, col[3] = {so.col[0], so.col[1], so.col[2]};
-                if (kr != kstop) Tk = Tk1 / (1.0f - alpha);
+                // T_k = T_{k+1} / (1 - alpha_k); Tk still holds T_{k+1} here, which a zero
+                // alpha leaves unchanged (x / 1 = x), so the division is skipped then
+                if (kr != kstop && alpha != 0.0f) Tk = Tk1 / (1.0f - alpha);
                 const float da = Tk * (fmaf(dC[0], col[0] - R0, fmaf(dC[1], col[1] - R1, dC[2] * (col[2] - R2))) +
                                        g4.w * P);
                 if (so.c.w == 0.0f) {
