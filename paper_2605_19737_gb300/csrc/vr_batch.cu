@@ -45,7 +45,7 @@ __device__ __forceinline__ void batch_body(const BatchLaunch& B) {
         unsigned dense = 0, evald = 0, shaded = 0, interp = 0;
         if (hit) {
             if (kAllDerived || v.dbricks)
-                march_gather<true, false, false, false, kBS>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r,
+                march_gather<true, false, false, true, kBS>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r,
                                                              B.skip, inv_gmax, is, out, dense, evald, shaded, interp);
             else
                 march_gather<false, false, false, true, kBS>(v, vw.tp, reinterpret_cast<const float4*>(vw.tf), r,
