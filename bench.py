@@ -215,8 +215,11 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
     ctx.precompute_morphology(vid)
     ctx.set_tissue_params(vid, case["tf"], **case["params"])
     out = torch.empty((cams.shape[0], H, W, 4), device=dev)
+    # the forward's brick size and launch shape tuned on the stateless render; the
+    # backward runs on the same bricks
+    shape, tuned = tune_case(ctx, vid, case, "diff_head128_8cam", out)
     ctr = pkg.new_counters(dev.index or 0)
-    ctx.render(vid, cams, W, H, out=out, counters=ctr)
+    ctx.render(vid, cams, W, H, out=out, counters=ctr, **shape)
     torch.cuda.synchronize()
     dense = int(ctr.cpu().numpy()[1])
     dl = torch.randn(out.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(20260523))
@@ -229,7 +232,7 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
         flush.zero_()
         s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         s0.record()
-        ctx.render(vid, cams, W, H, out=out, ray_state=state)
+        ctx.render(vid, cams, W, H, out=out, ray_state=state, **shape)
         s1.record()
         ctx.render_backward(vid, cams, W, H, dl, dtf=dtf, dparams=dpar, dvol=dvol, ray_state=state)
         s2.record()
@@ -239,22 +242,39 @@ def fwd_bwd_multiview(ctx, dev, flush, args):
     ctx.free_volume(vid)
     f_ms, b_ms = (float(np.mean([x[q] for x in ts])) for q in (0, 1))
     return {"workload": "diff_head128_8cam: 128^3 float32 head, 8 cameras, 512x512, 1D TF 256",
-            "dense_samples": dense, "fwd_ms": f_ms, "bwd_ms": b_ms,
+            "dense_samples": dense, "fwd_ms": f_ms, "bwd_ms": b_ms, "tuned": tuned,
             "fwd_gsamples_per_s": dense / (f_ms * 1e-3) / 1e9,
             "fwd_bwd_gsamples_per_s": dense / ((f_ms + b_ms) * 1e-3) / 1e9}
 
 
-def timed_view(ctx, vid, case, flush, args, kernel, label):
-    """Forward render of one named workload's views: CUDA-event time per frame (L2
-    flushed between frames), dense-equivalent Gsamples/s and FPS."""
+def tune_case(ctx, vid, case, key, out):
+    """Autotune one workload's single-call render (skip-brick edge x packet x CTA
+    size) on this GPU, leaving the chosen brick size set on the volume. Returns the
+    launch shape and the choice (without the per-candidate timings)."""
+    from paper_2605_19737_gb300 import autotune
+    n, H, W = case["cams"].shape[0], case["H"], case["W"]
+
+    def prepare(cells):
+        ctx.set_brick_size(vid, cells)
+        ctx.precompute_morphology(vid, case.get("sigmas", ()))
+        ctx.set_tissue_params(vid, case["tf"], **case["params"])
+    t = autotune.tune_render(ctx, vid, case["cams"], W, H, key, prepare=prepare, force=True, out=out)
+    return ({"packet_w": t["packet_w"], "warps_per_block": t["warps_per_block"]},
+            {k: t[k] for k in ("brick", "packet_w", "warps_per_block")})
+
+
+def timed_view(ctx, vid, case, flush, args, kernel, label, key):
+    """Forward render of one named workload's views at its autotuned launch: CUDA-event
+    time per frame (L2 flushed between frames), dense-equivalent Gsamples/s and FPS."""
     import torch
 
     import paper_2605_19737_gb300 as pkg
     dev = flush.device
     n, H, W = case["cams"].shape[0], case["H"], case["W"]
     out = torch.empty((n, H, W, 4), device=dev)
+    shape, tuned = tune_case(ctx, vid, case, key, out)
     ctr = pkg.new_counters(dev.index or 0)
-    ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, counters=ctr)
+    ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, counters=ctr, **shape)
     torch.cuda.synchronize()
     c = [int(x) for x in ctr.cpu().numpy()[:6]]
     ts = []
@@ -262,14 +282,14 @@ def timed_view(ctx, vid, case, flush, args, kernel, label):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
-        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel)
+        ctx.render(vid, case["cams"], W, H, out=out, kernel=kernel, **shape)
         e.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
             ts.append(s.elapsed_time(e))
     ms = float(np.mean(ts))
     return {"workload": label, "ms_per_frame": ms, "fps": 1000.0 * n / ms, "dense_samples": c[1],
-            "evaluated_samples": c[2], "gsamples_per_s": c[1] / (ms * 1e-3) / 1e9}
+            "evaluated_samples": c[2], "gsamples_per_s": c[1] / (ms * 1e-3) / 1e9, "tuned": tuned}
 
 
 def run_batched(args, ctx, dev, flush):
@@ -517,14 +537,15 @@ def run(args):
                       "ms": float(np.median(pre[1:]))}
         ctx.set_tissue_params(vvid, vcase["tf"], **vcase["params"])
         vessel = timed_view(ctx, vvid, vcase, flush, args, kernel,
-                            "vessel_1080p: 256x256x176 float32 vessel tree, 2D TF over (I, V), Phong, 1920x1080")
+                            "vessel_1080p: 256x256x176 float32 vessel tree, 2D TF over (I, V), Phong, 1920x1080",
+                            "vessel_1080p")
         ctx.free_volume(vvid)
         hcase = workloads.head64_128px()
         hvid = ctx.load_volume(torch.from_numpy(hcase["volume"]).to(dev), hcase["spacing"])
         ctx.precompute_morphology(hvid)
         ctx.set_tissue_params(hvid, hcase["tf"], **hcase["params"])
         head64 = timed_view(ctx, hvid, hcase, flush, args, kernel,
-                            "head64_128px: 64^3 float32 head, 1D TF, Phong, 128x128")
+                            "head64_128px: 64^3 float32 head, 1D TF, Phong, 128x128", "head64_128px")
         ctx.free_volume(hvid)
 
     batched = None if args.no_batch else run_batched(args, ctx, dev, flush)
