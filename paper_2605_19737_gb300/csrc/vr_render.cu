@@ -18,10 +18,10 @@ namespace {
 
 // Registers per thread: 64 for the derived-brick path (8 CTAs of 4 warps per SM:
 // equal at 1080p, 2.5 % faster on the 8-view 512^2 workload than 72), 72 when it also
-// records the ray state (64 would spill 64 bytes), 80 for the stencils. CTAs of 2, 4
-// or 8 warps (tile_pixel).
+// records the ray state (CTAs of at most 4 warps, 7 per SM: 1.5 % faster than 80 at 6;
+// 64 spills ~100 bytes), 80 for the stencils. CTAs of 2, 4 or 8 warps (tile_pixel).
 template <bool kDerived, bool kState, int kBS>
-__global__ void __launch_bounds__(256, kDerived ? (kState ? 3 : 4) : 3)
+__global__ void __launch_bounds__(kState ? 128 : 256, kDerived ? (kState ? 7 : 4) : (kState ? 6 : 3))
     k_render_gather(const __grid_constant__ RenderLaunch L) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int di, dj;
@@ -77,6 +77,9 @@ void launch_gather_bs(const RenderLaunch& L, dim3 grid, int threads, cudaStream_
 
 cudaError_t launch_render_gather(const RenderLaunch& L0, int warps, cudaStream_t st) {
     RenderLaunch L = L0;
+    // the state-recording kernels are built for CTAs of at most 4 warps (72 registers,
+    // 7 CTAs per SM); the image and the state do not depend on the CTA shape
+    if (L.ray_state && warps > 4) warps = 4;
     const int tx = tile_packets_x(L.packet_w, warps);
     L.tile_w = tx * L.packet_w;
     L.tile_h = (warps / tx) * L.packet_h;
