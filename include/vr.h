@@ -129,7 +129,9 @@ typedef struct {
                            per-lane kernels (default 4), also 32 for the staged and batched ones */
     int warps_per_block;/* warps per CTA: the per-lane kernels 2, 4 (default) or 8 -- their CTA
                            tile is min(warps, 16/packet_w) packets across and the rest down
-                           (4 warps: 16 x 8 pixels); the staged kernel 1..8 */
+                           (4 warps: 16 x 8 pixels); a render that records ray_state runs
+                           at most 4 (8 is taken as 4: the image is the same); the staged
+                           kernel 1..8 */
     void* ray_state;    /* NULL, or device memory of n_cams*H*W x 8 bytes (per-lane kernels
                            only): vr_render writes, per pixel, the index of the ray's last
                            sample (int32; -1 for none) and the transmittance in front of it
