@@ -43,8 +43,10 @@ struct TfGradSink {
     __device__ __forceinline__ TfGradSink(float* p_, bool two_d_) : p(p_), two_d(two_d_) {}
 
     __device__ __forceinline__ void put(int piece, const float4& v) const {
-        if (v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f)
-            atomicAdd(reinterpret_cast<float4*>(p + (size_t)key * kTfCellFloats) + piece, v);
+        // any component not +-0: one OR of the bit patterns, the sign bits shifted out
+        const unsigned bits = __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) |
+                              __float_as_uint(v.w);
+        if (bits << 1) atomicAdd(reinterpret_cast<float4*>(p + (size_t)key * kTfCellFloats) + piece, v);
     }
     __device__ __forceinline__ void flush() {
         if (key < 0) return;
