@@ -260,6 +260,21 @@ def test_zero_opacity_and_host_output(vr, torch):
     vr.free_volume(vid)
 
 
+def test_pinned_host_output_across_launches(vr, torch):
+    """More cameras than one launch takes (64): every launch writes its views straight
+    into the pinned host image at the right offset."""
+    case = workloads.head64_128px()
+    vid = _load_case(vr, torch, case)
+    cams = ph.camera_array([ph.orbit_camera(case["volume"].shape[::-1], case["spacing"], 5.0 * c, 10.0 - c * 0.3,
+                                            width=24, height=20) for c in range(70)])
+    dev = vr.render(vid, cams, 24, 20)
+    host = torch.full((70, 20, 24, 4), -1.0, dtype=torch.float32).pin_memory()
+    vr.render(vid, cams, 24, 20, out=host)
+    vr.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), host.numpy())
+    vr.free_volume(vid)
+
+
 def test_counters_match_ray_samples(vr, torch):
     import paper_2605_19737_gb300 as pkg
     case = workloads.head64_128px()
