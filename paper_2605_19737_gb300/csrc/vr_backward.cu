@@ -2,28 +2,30 @@
 // with respect to the transfer-function entries, the tissue uniforms
 // (gamma, ka, kd, ks, opacity_scale) and the normalised voxel intensities.
 //
-// One thread per ray (the forward kernel's 8x4 warp packets). Per ray:
-//   1. forward re-march with the forward kernel's exact arithmetic (empty bricks
-//      skipped), recording the stopping sample k_stop and the transmittance T
-//      before it;
-//   2. reverse sweep over every sample k = k_stop .. 0 (no skipping: the opacity
-//      entries of the transfer function receive gradient from samples whose
-//      opacity is zero) with no stored samples: the sample is re-evaluated,
-//      T_k = T_{k+1} / (1 - alpha_k) (exact in real arithmetic and well
-//      conditioned because early termination keeps 1 - alpha_k >= 1 - et
-//      before the last sample), R_k = alpha_k c_k + (1 - alpha_k) R_{k+1} and
-//      P_k = prod_{j>k} (1 - alpha_j) are carried backwards, and
+// One thread per ray (the forward kernel's warp packets, 4 warps per CTA). Per ray:
+//   1. the ray's stopping sample k_stop and the transmittance T in front of it, from
+//      the forward's ray state, or by a forward re-march with the forward kernel's
+//      exact arithmetic (empty bricks skipped);
+//   2. reverse sweep over every sample k = k_stop .. 0, the lanes of a warp in step
+//      by sample index (no skipping: the opacity entries of the transfer function
+//      receive gradient from samples whose opacity is zero) with no stored samples:
+//      the sample is re-evaluated, T_k = T_{k+1} / (1 - alpha_k) (exact in real
+//      arithmetic and well conditioned because early termination keeps
+//      1 - alpha_k >= 1 - et before the last sample), R_k = alpha_k c_k +
+//      (1 - alpha_k) R_{k+1} and P_k = prod_{j>k} (1 - alpha_j) are carried
+//      backwards, and
 //        dL/dalpha_k = T_k (<dL/dC, c_k - R_{k+1}> + dL/dA P_k),
 //        dL/dc_k     = T_k alpha_k dL/dC              (Eqs. 5-6 differentiated);
 //   3. sample_adjoint / field_adjoint_scatter chain these to the parameters.
 // Transfer-function gradients are accumulated per lane while its samples stay in
-// one transfer-function cell, then added with 16-byte vector atomics into 64
-// private global copies of the table (CTA c into copy c % 64) that k_sum_copies
-// adds up afterwards -- contended atomics on one 256 KB table cost 10x the rest
-// of the kernel, and a shared-memory table per CTA (1D tables) 1.6x the copies. Voxel gradients: on the derived bricks, per-
-// voxel channel gradients (vector atomics) and a gather pass through the stencil
-// transposes; otherwise scalar global atomics on the voxels. Uniform gradients are
-// warp-reduced first.
+// one lookup cell, then added with 16-byte vector atomics into private global
+// copies of the gradient (one 16-float record per cell; CTA c into copy c % n) that
+// k_sum_copies gathers afterwards -- contended atomics on one table cost 10x the
+// rest of the kernel, and a shared-memory table per CTA 1.6x (1D) to 1.8x (2D
+// opacities) the copies. Voxel gradients: on the derived bricks, per-voxel channel
+// gradients (vector atomics, neighbouring lanes in one cell merged, corner order
+// rotated) and a gather pass through the stencil transposes; otherwise scalar
+// global atomics on the voxels. Uniform gradients are warp-reduced first.
 #include "vr_adjoint.cuh"
 
 namespace vr {
